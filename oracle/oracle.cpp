@@ -224,7 +224,8 @@ static int remove_test(i64 K, i64 V, i64 d, i64 k, double alpha, int *path, bool
 // f = K u / (V u)^alpha with u = 2^unit_exp (Eq. 1 in original weight units).
 static double fitness(i64 K, i64 V, double alpha, int unit_exp) {
     if (K == 0) return 0.0;
-    quad lf = q_log((quad)K) - (quad)alpha * q_log((quad)V) + (quad)(1.0 - alpha) * (quad)unit_exp * q_log((quad)2);
+    quad a = (quad)alpha;
+    quad lf = q_log((quad)K) - a * q_log((quad)V) + ((quad)1 - a) * (quad)unit_exp * q_log((quad)2);
     return (double)q_exp(lf);
 }
 

@@ -1,0 +1,235 @@
+"""Pins for the oracle's community growth (Alg. 1 repeated as in Alg. 2, Eq. 1-2).
+
+What fixes the expected values here, independently of the oracle:
+* hand traces of Alg. 1 on small graphs (tests/golden/hand_traces.json);
+* closed forms of Eq. 1 on cliques and stars;
+* brute force over every subset of <= 12-node graphs, with f compared exactly
+  (big integers for dyadic alpha, 300-bit mpmath otherwise): the result is a
+  local optimum for single additions and single non-seed removals, and equals
+  the global optimum where the seed's component is a clique;
+* invariants: the seed is always a member; results do not depend on the
+  number of threads;
+* planted recovery on the 1,000-node planted partition: the micro and macro
+  communities appear at different scales.
+"""
+import itertools
+import json
+import math
+import os
+import random
+
+import numpy as np
+import pytest
+
+from paper_1301_0955_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def graph_from_edges(orc, n, edges, w=None):
+    e = np.asarray(edges, np.int64).reshape(-1, 2)
+    rp, col, ww = synth.to_csr(n, e[:, 0], e[:, 1], None if w is None else np.asarray(w, np.float32))
+    g = orc.Graph(n, rp, col, ww)
+    assert g.status == 0
+    return g, rp, col
+
+
+@pytest.mark.parametrize("case", json.load(open(os.path.join(HERE, "golden", "hand_traces.json")))["cases"],
+                         ids=lambda c: c["name"])
+def test_hand_traces(orc, case):
+    g, _, _ = graph_from_edges(orc, case["n"], case["edges"])
+    mem, f, st, rc = orc.grow(g, case["seed"], case["alpha"])
+    assert rc == 0
+    assert mem.tolist() == case["members"]
+    assert st["K"] == case["K"] and st["V"] == case["V"]
+    assert f == pytest.approx(case["f"], rel=1e-15)
+    for key in ("edges_scanned", "adds", "removes", "rounds"):
+        assert st[key] == case[key], key
+
+
+@pytest.mark.parametrize("m", [2, 3, 5, 8, 13])
+@pytest.mark.parametrize("alpha", [0.5, 0.7, 1.0, 1.3])
+def test_clique_closed_form(orc, m, alpha):
+    """A clique with no outside edges is grown whole: K = V = m(m-1), f = (m(m-1))^(1-alpha)."""
+    edges = list(itertools.combinations(range(m), 2))
+    g, _, _ = graph_from_edges(orc, m, edges)
+    for seed in range(m):
+        mem, f, st, rc = orc.grow(g, seed, alpha)
+        assert rc == 0 and mem.tolist() == list(range(m))
+        assert st["K"] == m * (m - 1) == st["V"]
+        assert f == pytest.approx((m * (m - 1)) ** (1 - alpha), rel=1e-15)
+
+
+@pytest.mark.parametrize("m", [1, 2, 6, 20])
+@pytest.mark.parametrize("alpha", [0.5, 0.8, 1.0])
+def test_star_closed_form(orc, m, alpha):
+    """From the centre of a star with m leaves and alpha <= 1 every leaf joins
+    ((1+1/j) > (1+1/(m+j))^alpha), f = 2m / (2m)^alpha."""
+    edges = [(0, i) for i in range(1, m + 1)]
+    g, _, _ = graph_from_edges(orc, m + 1, edges)
+    mem, f, st, rc = orc.grow(g, 0, alpha)
+    assert mem.tolist() == list(range(m + 1))
+    assert f == pytest.approx((2 * m) ** (1 - alpha), rel=1e-15)
+
+
+def test_isolated_seed(orc):
+    g, _, _ = graph_from_edges(orc, 3, [(1, 2)])
+    mem, f, st, rc = orc.grow(g, 0, 0.7)
+    assert rc == 0 and mem.tolist() == [0] and f == 0.0 and st["V"] == 0
+
+
+def test_weighted_closed_form(orc):
+    """Weighted clique with no outside edges at alpha = 1: f = 1 in any unit."""
+    edges = list(itertools.combinations(range(5), 2))
+    rng = np.random.default_rng(0)
+    w = rng.uniform(0.5, 2.0, len(edges)).astype(np.float32)
+    g, _, _ = graph_from_edges(orc, 5, edges, w)
+    mem, f, st, rc = orc.grow(g, 2, 1.0)
+    assert mem.tolist() == [0, 1, 2, 3, 4] and f == pytest.approx(1.0, rel=1e-15)
+
+
+# ---------------------------------------------------------------- brute force
+
+DYADIC = {1.0: (1, 0), 0.5: (1, 1), 0.75: (3, 2), 0.625: (5, 3)}
+
+
+def f_greater(K1, V1, K2, V2, alpha):
+    """Exact test K1/V1^alpha > K2/V2^alpha (f = 0 when K = 0)."""
+    if K1 == 0:
+        return False
+    if K2 == 0:
+        return True
+    if alpha in DYADIC:
+        P, s = DYADIC[alpha]
+        return K1 ** (2 ** s) * V2 ** P > K2 ** (2 ** s) * V1 ** P
+    mpmath = pytest.importorskip("mpmath")
+    with mpmath.workprec(300):
+        d = mpmath.log(K1) - mpmath.log(K2) - mpmath.mpf(alpha) * (mpmath.log(V1) - mpmath.log(V2))
+        return d > mpmath.mpf(2) ** -250
+
+
+def kv(adj_w, k, members):
+    K = sum(adj_w[u].get(v, 0) for u in members for v in members if u != v)
+    V = sum(k[u] for u in members)
+    return K, V
+
+
+def random_small_graph(rng, n, p, weighted=False):
+    edges = [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < p]
+    w = [rng.randint(1, 4) for _ in edges] if weighted else None
+    return edges, w
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.5, 0.75, 0.625, 0.6180339887498949])
+def test_bruteforce_local_optimum(orc, alpha):
+    rng = random.Random(int(alpha * 1000))
+    checked = 0
+    for it in range(60):
+        n = rng.randint(4, 12)
+        weighted = it % 3 == 2
+        edges, w = random_small_graph(rng, n, rng.uniform(0.2, 0.6), weighted)
+        if not edges:
+            continue
+        g, rp, col = graph_from_edges(orc, n, edges, w)
+        adj = [dict() for _ in range(n)]
+        for idx, (a, b) in enumerate(edges):
+            ww = 1 if w is None else w[idx]
+            adj[a][b] = ww
+            adj[b][a] = ww
+        k = [sum(adj[u].values()) for u in range(n)]
+        for seed in range(n):
+            mem, f, st, rc = orc.grow(g, seed, alpha)
+            assert rc == 0
+            c = set(mem.tolist())
+            assert seed in c
+            K, V = kv(adj, k, c)
+            unit = 2.0 ** g.info()["unit_exp"]
+            assert (K, V) == (st["K"] * unit, st["V"] * unit)
+            if K:
+                assert f == pytest.approx(K / V ** alpha, rel=1e-14)
+            for u in range(n):
+                if u in c:
+                    if u == seed:
+                        continue
+                    K2, V2 = kv(adj, k, c - {u})
+                else:
+                    K2, V2 = kv(adj, k, c | {u})
+                assert not f_greater(K2, V2, K, V, alpha), (edges, seed, alpha, sorted(c), u)
+            # global optimum over subsets containing the seed bounds the result
+            others = [u for u in range(n) if u != seed]
+            if n <= 10:
+                best = (0, 1)
+                for r in range(len(others) + 1):
+                    for sub in itertools.combinations(others, r):
+                        K2, V2 = kv(adj, k, set(sub) | {seed})
+                        if f_greater(K2, V2, *best, alpha):
+                            best = (K2, V2)
+                assert not f_greater(K, V, *best, alpha)
+            checked += 1
+    assert checked > 200
+
+
+@pytest.mark.parametrize("alpha", [0.5, 0.75, 1.0])
+def test_disjoint_cliques_reach_global_optimum(orc, alpha):
+    """The seed's component is a clique: growth returns exactly that clique, the
+    global optimum over subsets containing the seed."""
+    sizes = [3, 5, 2, 4]
+    edges, base = [], 0
+    for m in sizes:
+        edges += [(base + i, base + j) for i, j in itertools.combinations(range(m), 2)]
+        base += m
+    g, _, _ = graph_from_edges(orc, base, edges)
+    base = 0
+    for m in sizes:
+        for seed in range(base, base + m):
+            mem, f, st, rc = orc.grow(g, seed, alpha)
+            assert mem.tolist() == list(range(base, base + m))
+        base += m
+
+
+def test_thread_count_independent(orc):
+    g0 = synth.config_graph(0)
+    g = orc.Graph(g0.n, g0.row_ptr, g0.col)
+    alphas = [1.0, 0.7, 0.5]
+    seeds = np.arange(0, 1000, 7, dtype=np.int32)
+    r1 = orc.run(g, alphas, seeds, threads=1)
+    r4 = orc.run(g, alphas, seeds, threads=4)
+    assert r1[0] == 0 and r4[0] == 0
+    for a, b in zip(r1[1:], r4[1:]):
+        assert np.array_equal(a, b)
+
+
+def jaccard_best(found, planted):
+    out = []
+    for P in planted:
+        best = 0.0
+        for C in found:
+            inter = len(P & C)
+            if inter:
+                best = max(best, inter / len(P | C))
+        out.append(best)
+    return float(np.mean(out))
+
+
+def test_planted_recovery(orc):
+    """1,000-node planted partition: some scale recovers the 20 communities and a
+    coarser one the 4 super-groups (the paper's Table 1 shows the same two-band
+    behaviour on its hierarchical benchmark)."""
+    g0 = synth.config_graph(0)
+    g = orc.Graph(g0.n, g0.row_ptr, g0.col)
+    rc, alphas = orc.scales_logspaced(0.5, 1.0, 8)
+    rc, ptr, nodes, f, st = orc.run(g, alphas, threads=8)
+    assert rc == 0
+    micro = [set(np.flatnonzero(g0.labels[0] == c).tolist()) for c in range(20)]
+    macro = [set(np.flatnonzero(g0.labels[1] == c).tolist()) for c in range(4)]
+    best_micro = best_macro = 0.0
+    for s in range(8):
+        sl = slice(s * 1000, (s + 1) * 1000 + 1)
+        p = ptr[sl] - ptr[s * 1000]
+        cptr, cnodes, u2c, first = orc.unique_communities(p, nodes[ptr[s * 1000]:ptr[(s + 1) * 1000]])
+        found = [set(cnodes[cptr[i]:cptr[i + 1]].tolist()) for i in range(len(cptr) - 1)]
+        jm = min(jaccard_best(micro, found), jaccard_best(found, micro))
+        jM = min(jaccard_best(macro, found), jaccard_best(found, macro))
+        best_micro, best_macro = max(best_micro, jm), max(best_macro, jM)
+    assert best_micro >= 0.9
+    assert best_macro >= 0.9
