@@ -1,0 +1,191 @@
+/*
+ * mscd.h — C ABI of the GB300 multi-scale local-criterion community growth
+ * library (libmscd.so).
+ *
+ * The method is that of Le Martelot & Hankin, "Fast Multi-Scale Community
+ * Detection based on Local Criteria within a Multi-Threaded Algorithm":
+ * for every scale alpha and every seed node, a community grows from {seed}
+ * by the greedy rule of Algorithm 1 (max priority queue ranked by
+ * 2 d_in / (d_in + d_out)^alpha, add a node iff it raises the LFK fitness
+ * f_c = k_in / (k_in + k_out)^alpha of Eq. 1, Eq. 2 as a strict test, then
+ * prune members whose removal raises f), repeated while a grow pass adds
+ * something ("while changes can be made", Algorithm 2).  Identical
+ * communities found from different seeds are deduplicated per scale, and
+ * successive scales are compared with the overlapping NMI cited in Sec. 4,
+ * averaged over windows of 3 and 5 scales.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: MSCD_OK (0) or a negative code
+ *     below; mscd_strerror() gives its text.  Nothing is fixed silently.
+ *   - Array arguments are host pointers unless a function takes `flags` and
+ *     MSCD_DEVICE_PTRS is set, in which case they are device pointers on the
+ *     context's device.  Input arrays are copied before the call returns; the
+ *     caller keeps ownership of everything it passes.
+ *   - Outputs go to caller-owned buffers.  A buffer that is too small gives
+ *     MSCD_ESMALL with the required length written back; cap = 0 queries it.
+ *   - A context is not thread-safe: calls on one context must not overlap.
+ *   - Exact decisions: every add / remove / priority decision is the exact
+ *     sign of log(a1/a2) - alpha*log(b1/b2) over integer operands (weights
+ *     are converted exactly to int64 multiples of the largest power of two
+ *     dividing all of them), so memberships are independent of thread, warp
+ *     and launch order.
+ */
+#ifndef MSCD_H
+#define MSCD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MSCD_OK 0
+#define MSCD_EINVAL (-1)      /* bad argument or malformed CSR structure          */
+#define MSCD_ENOTSYM (-2)     /* CSR not symmetric, or unequal weights u->v, v->u */
+#define MSCD_ESELFLOOP (-3)   /* an entry u -> u                                  */
+#define MSCD_EDUP (-4)        /* a repeated entry inside one row                  */
+#define MSCD_ERANGE (-5)      /* exact fixed-point weights need more than 62 bits */
+#define MSCD_ENOMEM (-6)      /* device allocation failed                         */
+#define MSCD_EDEVICE (-7)     /* CUDA error (device, launch or copy)              */
+#define MSCD_ETIMEOUT (-8)    /* a unit hit the grow/prune repetition cap         */
+#define MSCD_ESMALL (-9)      /* output buffer too small; length written back     */
+#define MSCD_EUNDECIDED (-10) /* a decision no certified stage could settle       */
+#define MSCD_EUNSORTED (-11)  /* a CSR row is not in ascending column order       */
+#define MSCD_EWEIGHT (-12)    /* a weight that is not finite and > 0              */
+#define MSCD_ENORESULT (-13)  /* no successful run to read results from           */
+
+/* ---- flags ------------------------------------------------------------- */
+#define MSCD_DEVICE_PTRS 1u   /* array arguments are device pointers             */
+
+/* Per-unit statistics (int64 each, in this order): CSR entries scanned
+ * (seed row + rows of every added and removed node), nodes added, nodes
+ * removed, grow/prune rounds, final K (internal degree sum, weight units),
+ * final V (volume, weight units), decisions taken by a slow stage, undecided
+ * flag. */
+#define MSCD_STAT_EDGES 0
+#define MSCD_STAT_ADDS 1
+#define MSCD_STAT_REMOVES 2
+#define MSCD_STAT_ROUNDS 3
+#define MSCD_STAT_K 4
+#define MSCD_STAT_V 5
+#define MSCD_STAT_SLOW 6
+#define MSCD_STAT_UNDECIDED 7
+#define MSCD_NSTATS 8
+
+typedef struct mscd_ctx mscd_ctx;
+
+/* Tuning and limits.  Zero fields take the defaults. */
+typedef struct mscd_params {
+    int32_t struct_size;     /* sizeof(mscd_params)                                  */
+    int32_t warps_per_block; /* growth kernel: warps per CTA, one unit per warp (8)   */
+    int32_t smem_slots;      /* node slots per warp in shared memory (512, power of 2) */
+    int32_t blocks_per_sm;   /* persistent growth grid: CTAs per SM (from occupancy)   */
+    int64_t max_rounds;      /* grow/prune repetitions per unit before ETIMEOUT (1e6)  */
+} mscd_params;
+
+/* Totals of the last run. */
+typedef struct mscd_run_stats {
+    int64_t units;            /* (scale, seed) units grown                         */
+    int64_t edges_scanned;    /* sum of MSCD_STAT_EDGES                            */
+    int64_t adds, removes;    /* sums over units                                   */
+    int64_t slow_decisions;   /* decisions settled by the tie test or double-double */
+    int64_t undecided;        /* units with an undecided decision (expected 0)     */
+    int64_t overflow_units;   /* units re-grown in a larger node-slot class        */
+    int64_t grow_launches;    /* growth kernel launches                            */
+    int64_t member_entries;   /* total member-list length over all units           */
+    double ms_grow, ms_dedup, ms_stability, ms_total; /* device time per stage    */
+} mscd_run_stats;
+
+/* Text of a status code (static storage). */
+const char *mscd_strerror(int status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int mscd_version(void);
+
+/* Create a context on CUDA device `device`.  params may be NULL.  Errors:
+ * EINVAL (bad device or params), EDEVICE, ENOMEM. */
+int mscd_create(mscd_ctx **out, int device, const mscd_params *params);
+
+/* Free a context and every graph and result it holds. */
+int mscd_destroy(mscd_ctx *ctx);
+
+/* Load an undirected graph in CSR form (the paper's input network, Alg. 2).
+ *   n        number of nodes (0 <= n < 2^31)
+ *   row_ptr  int64[n+1], row_ptr[0] = 0, non-decreasing
+ *   col      int32[row_ptr[n]], each row strictly ascending, no u -> u
+ *   w        float32[row_ptr[n]] edge weights (finite, > 0), or NULL for an
+ *            unweighted graph (every weight 1)
+ * The CSR must be symmetric with equal weights in both directions.  Checks
+ * run on the device in a fixed category order and the first failing
+ * category is returned: EINVAL (structure), EWEIGHT, ESELFLOOP, EUNSORTED,
+ * EDUP, ENOTSYM, ERANGE.  On success *graph_id names the resident graph
+ * (arrays copied to device memory; degrees and exact weights precomputed). */
+int mscd_graph_load_csr(mscd_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                        const float *w, uint32_t flags, int32_t *graph_id);
+
+/* Release a resident graph.  EINVAL for an unknown id. */
+int mscd_graph_free(mscd_ctx *ctx, int32_t graph_id);
+
+/* Facts of a resident graph: node and entry counts, the weight unit 2^unit_exp
+ * of the exact fixed-point weights, total volume in weight units. */
+int mscd_graph_info(mscd_ctx *ctx, int32_t graph_id, int64_t *n, int64_t *nnz, int32_t *unit_exp,
+                    int64_t *volume);
+
+/* Weighted degrees k_u in weight units, host int64[n]. */
+int mscd_graph_degrees(mscd_ctx *ctx, int32_t graph_id, int64_t *k);
+
+/* The logarithmic scale list of Sec. 4, read as
+ *   alpha_k = vmin + (a - vmin) (1 - log k / log x),  k = 1..x,
+ * i.e. a first (finest scale, smallest communities) down to vmin (coarsest);
+ * x = 1 gives {a}.  out: host double[x].  EINVAL unless x >= 1, 0 < vmin <= a. */
+int mscd_scales_logspaced(double vmin, double a, int32_t x, double *out);
+
+/* Grow one community per (scale, seed) unit, deduplicate per scale and compare
+ * successive scales (Alg. 1 per unit, Sec. 4 for the stability measure).
+ *   alphas   double[n_scales], each finite and > 0 (ordered as the caller wants
+ *            successive scales compared; Sec. 4 lists them fine to coarse)
+ *   seeds    int32[n_seeds] node ids, or NULL for every node (n_seeds ignored)
+ *   flags    MSCD_DEVICE_PTRS: alphas and seeds are device pointers
+ *   cuda_stream  cudaStream_t to order the work on, or NULL for the context's
+ * Synchronous: returns when results are ready.  Unit index = scale * n_seeds +
+ * seed index.  Errors: EINVAL, ENOMEM, EDEVICE; ETIMEOUT or EUNDECIDED when a
+ * unit hit the round cap or an undecided comparison (results still readable,
+ * the unit's statistics say which). */
+int mscd_run(mscd_ctx *ctx, int32_t graph_id, const double *alphas, int32_t n_scales, const int32_t *seeds,
+             int64_t n_seeds, uint32_t flags, void *cuda_stream);
+
+/* Membership of one unit: the sorted member list (host int32, cap entries),
+ * its length and its fitness f (Eq. 1 in the original weight units). */
+int mscd_get_membership(mscd_ctx *ctx, int32_t scale_idx, int64_t seed_idx, int32_t *buf, int64_t cap,
+                        int64_t *len, double *fitness);
+
+/* All memberships of one scale, concatenated in seed order: ptr int64[n_seeds+1],
+ * nodes int32[nodes_cap], fitness double[n_seeds] (may be NULL), stats
+ * int64[n_seeds * MSCD_NSTATS] (may be NULL).  *n_nodes gets the total length. */
+int mscd_get_memberships(mscd_ctx *ctx, int32_t scale_idx, int64_t *ptr, int32_t *nodes, int64_t nodes_cap,
+                         double *fitness, int64_t *stats, int64_t *n_nodes);
+
+/* Deduplicated communities of one scale, numbered in order of their smallest
+ * generating seed index: ptr int64[n_comms+1] (ptr_cap entries), nodes
+ * int32[nodes_cap], fitness double[n_comms] (may be NULL), seed2comm
+ * int32[n_seeds] (may be NULL).  *n_comms and *n_nodes get the sizes. */
+int mscd_get_communities(mscd_ctx *ctx, int32_t scale_idx, int64_t *ptr, int64_t ptr_cap, int32_t *nodes,
+                         int64_t nodes_cap, double *fitness, int32_t *seed2comm, int64_t *n_comms,
+                         int64_t *n_nodes);
+
+/* Stability across scales (Sec. 4): nmi_succ double[n_scales-1] with the
+ * overlapping NMI between deduplicated sets of scales i and i+1; nmi_win3 and
+ * nmi_win5 double[n_scales] with its mean over the window of 3 (5) scales
+ * centred on scale i (clipped at the ends; NaN when the window holds no pair).
+ * Any pointer may be NULL. */
+int mscd_get_stability(mscd_ctx *ctx, double *nmi_succ, double *nmi_win3, double *nmi_win5);
+
+/* Totals of the last run. */
+int mscd_get_run_stats(mscd_ctx *ctx, mscd_run_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSCD_H */

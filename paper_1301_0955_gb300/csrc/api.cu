@@ -1,0 +1,673 @@
+// C ABI of the library (declared in include/mscd.h).
+//
+// A context owns its resident graphs, the results of its last run and a
+// reusable growth arena.  mscd_run grows every (scale, seed) unit with the
+// growth kernel (first in the shared-memory slot class, then units that
+// outgrew it in larger global-memory classes, until the class holds every
+// node), deduplicates each scale and measures the stability between
+// successive scales.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "dedup.cuh"
+#include "grow.cuh"
+
+namespace {
+
+struct GraphRec {
+    bool live = false;
+    i64 *rp = nullptr;
+    i32 *col = nullptr;
+    float *w = nullptr;
+    i64 *wfx = nullptr, *k = nullptr;
+    double *logk = nullptr;
+    DevGraph g;
+};
+
+struct Counters {
+    unsigned long long work, out_cursor, out_needed, n_retry_state, n_retry_out;
+    u32 error_flags;
+    u32 pad;
+};
+
+__global__ void check_seeds(const i32 *seeds, i64 N, i64 n, u32 *bad) {
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (i64)gridDim.x * blockDim.x)
+        if (seeds[i] < 0 || (i64)seeds[i] >= n) atomicOr(bad, 1u);
+}
+
+// Column sums of the per-unit statistics and status counts.
+__global__ void sum_unit_stats(const i64 *ustat, const i32 *ulen, const i32 *ustatus, i64 U,
+                               unsigned long long *tot) {
+    unsigned long long s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long ntime = 0, nund = 0, len = 0;
+    for (i64 u = (i64)blockIdx.x * blockDim.x + threadIdx.x; u < U; u += (i64)gridDim.x * blockDim.x) {
+        const i64 *r = ustat + u * MSCD_NSTATS;
+        s[0] += r[MSCD_STAT_EDGES];
+        s[1] += r[MSCD_STAT_ADDS];
+        s[2] += r[MSCD_STAT_REMOVES];
+        s[3] += r[MSCD_STAT_SLOW];
+        s[4] += r[MSCD_STAT_UNDECIDED];
+        len += ulen[u];
+        ntime += ustatus[u] == MSCD_ETIMEOUT;
+        nund += ustatus[u] == MSCD_EUNDECIDED;
+    }
+    s[5] = ntime;
+    s[6] = nund;
+    s[7] = len;
+    for (int j = 0; j < 8; ++j) {
+        unsigned long long v = s[j];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&tot[j], v);
+    }
+}
+
+__global__ void gather_lists(const i64 *uoff, const i32 *ulen, const i64 *dst_ptr, const i32 *nodes, i64 N,
+                             i32 *dst) {
+    const int lane = threadIdx.x & 31;
+    const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
+    for (i64 u = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < N; u += warps) {
+        const i32 *src = nodes + uoff[u];
+        i32 *d = dst + dst_ptr[u];
+        for (int i = lane; i < ulen[u]; i += 32) d[i] = src[i];
+    }
+}
+
+__global__ void widen_len(const i32 *ulen, i64 N, i64 *out) {
+    for (i64 u = (i64)blockIdx.x * blockDim.x + threadIdx.x; u < N; u += (i64)gridDim.x * blockDim.x) out[u] = ulen[u];
+}
+
+}  // namespace
+
+struct mscd_ctx {
+    int device = 0;
+    int sm_count = 1;
+    mscd_params p{};
+    cudaStream_t own = nullptr;
+    std::vector<GraphRec> graphs;
+    // last run
+    bool have = false;
+    int32_t S = 0;
+    i64 N = 0, U = 0, n_nodes_graph = 0;
+    double *alphas = nullptr;
+    i32 *seeds = nullptr;
+    i64 *uoff = nullptr;
+    i32 *ulen = nullptr;
+    u64 *uhash = nullptr;
+    double *uf = nullptr;
+    i64 *ustat = nullptr;
+    i32 *ustatus = nullptr;
+    i32 *out_nodes = nullptr;
+    i64 out_cap = 0;
+    std::vector<ScaleResult> scales;
+    std::vector<double> nmi_succ, win3, win5;
+    mscd_run_stats stats{};
+    // reusable growth arena
+    unsigned char *arena = nullptr;
+    size_t arena_bytes = 0;
+};
+
+namespace {
+
+void free_run(mscd_ctx *c) {
+    cudaFree(c->alphas);
+    cudaFree(c->seeds);
+    cudaFree(c->uoff);
+    cudaFree(c->ulen);
+    cudaFree(c->uhash);
+    cudaFree(c->uf);
+    cudaFree(c->ustat);
+    cudaFree(c->ustatus);
+    cudaFree(c->out_nodes);
+    c->alphas = nullptr;
+    c->seeds = nullptr;
+    c->uoff = nullptr;
+    c->ulen = nullptr;
+    c->uhash = nullptr;
+    c->uf = nullptr;
+    c->ustat = nullptr;
+    c->ustatus = nullptr;
+    c->out_nodes = nullptr;
+    c->out_cap = 0;
+    for (auto &s : c->scales) scale_result_free(&s);
+    c->scales.clear();
+    c->nmi_succ.clear();
+    c->win3.clear();
+    c->win5.clear();
+    c->have = false;
+}
+
+void free_graph(GraphRec &g) {
+    cudaFree(g.rp);
+    cudaFree(g.col);
+    cudaFree(g.w);
+    cudaFree(g.wfx);
+    cudaFree(g.k);
+    cudaFree(g.logk);
+    g = GraphRec{};
+}
+
+GraphRec *find_graph(mscd_ctx *c, int32_t id) {
+    if (!c || id < 0 || id >= (int32_t)c->graphs.size() || !c->graphs[id].live) return nullptr;
+    return &c->graphs[id];
+}
+
+int ensure_arena(mscd_ctx *c, size_t bytes) {
+    if (c->arena_bytes >= bytes) return MSCD_OK;
+    cudaFree(c->arena);
+    c->arena = nullptr;
+    c->arena_bytes = 0;
+    MSCD_CUDA(cudaMalloc((void **)&c->arena, bytes));
+    c->arena_bytes = bytes;
+    return MSCD_OK;
+}
+
+// Enlarge the unit output buffer, keeping what was written.
+int grow_output(mscd_ctx *c, i64 need, cudaStream_t st) {
+    if (need <= c->out_cap) return MSCD_OK;
+    i64 cap = std::max<i64>(need + need / 4, 2 * c->out_cap);
+    i32 *nb = nullptr;
+    MSCD_CUDA(cudaMalloc((void **)&nb, (size_t)cap * sizeof(i32)));
+    if (c->out_nodes && c->out_cap > 0)
+        MSCD_CUDA(cudaMemcpyAsync(nb, c->out_nodes, (size_t)c->out_cap * sizeof(i32), cudaMemcpyDeviceToDevice, st));
+    MSCD_CUDA(cudaStreamSynchronize(st));
+    cudaFree(c->out_nodes);
+    c->out_nodes = nb;
+    c->out_cap = cap;
+    return MSCD_OK;
+}
+
+void window_means(const std::vector<double> &nmi, int32_t S, int p, std::vector<double> &out) {
+    out.assign(S, NAN);
+    for (int32_t i = 0; i < S; ++i) {
+        int32_t lo = i - (p - 1) / 2, hi = lo + p - 1;
+        lo = std::max(lo, 0);
+        hi = std::min(hi, S - 1);
+        double s = 0.0;
+        int cnt = 0;
+        for (int32_t j = lo; j + 1 <= hi; ++j) {
+            s += nmi[j];
+            ++cnt;
+        }
+        out[i] = cnt ? s / cnt : NAN;
+    }
+}
+
+struct Task {
+    int cap;
+    std::vector<i64> units;  // empty + all = every unit
+    bool all;
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *mscd_strerror(int s) {
+    switch (s) {
+    case MSCD_OK: return "ok";
+    case MSCD_EINVAL: return "invalid argument or malformed CSR structure";
+    case MSCD_ENOTSYM: return "CSR is not symmetric (missing reverse entry or unequal weight)";
+    case MSCD_ESELFLOOP: return "CSR has a self-loop";
+    case MSCD_EDUP: return "CSR row has a repeated entry";
+    case MSCD_ERANGE: return "exact fixed-point weights exceed 62 bits";
+    case MSCD_ENOMEM: return "device memory allocation failed";
+    case MSCD_EDEVICE: return "CUDA device error";
+    case MSCD_ETIMEOUT: return "a unit hit the grow/prune repetition cap";
+    case MSCD_ESMALL: return "output buffer too small";
+    case MSCD_EUNDECIDED: return "a comparison could not be decided by any certified stage";
+    case MSCD_EUNSORTED: return "CSR row not in ascending column order";
+    case MSCD_EWEIGHT: return "edge weight not finite and positive";
+    case MSCD_ENORESULT: return "no successful run to read results from";
+    default: return "unknown status";
+    }
+}
+
+int mscd_version(void) { return 100; }
+
+int mscd_create(mscd_ctx **out, int device, const mscd_params *params) {
+    if (!out) return MSCD_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return MSCD_EDEVICE;
+    if (device < 0 || device >= ndev) return MSCD_EINVAL;
+    if (params && params->struct_size != (int32_t)sizeof(mscd_params)) return MSCD_EINVAL;
+    MSCD_CUDA(cudaSetDevice(device));
+    mscd_ctx *c = new (std::nothrow) mscd_ctx();
+    if (!c) return MSCD_ENOMEM;
+    c->device = device;
+    if (params) c->p = *params;
+    if (c->p.warps_per_block <= 0) c->p.warps_per_block = 8;
+    if (c->p.smem_slots <= 0) c->p.smem_slots = 512;
+    if (c->p.max_rounds <= 0) c->p.max_rounds = 1000000;
+    if (c->p.warps_per_block > GROW_MAX_THREADS / 32 || (c->p.smem_slots & (c->p.smem_slots - 1)) ||
+        c->p.smem_slots < 32) {
+        delete c;
+        return MSCD_EINVAL;
+    }
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return MSCD_EDEVICE;
+    }
+    *out = c;
+    return MSCD_OK;
+}
+
+int mscd_destroy(mscd_ctx *c) {
+    if (!c) return MSCD_EINVAL;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->own);
+    free_run(c);
+    for (auto &g : c->graphs) free_graph(g);
+    cudaFree(c->arena);
+    cudaStreamDestroy(c->own);
+    delete c;
+    return MSCD_OK;
+}
+
+int mscd_graph_load_csr(mscd_ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col, const float *w,
+                        uint32_t flags, int32_t *graph_id) {
+    if (!c || !row_ptr || !graph_id || n < 0 || n >= (int64_t)INT32_MAX) return MSCD_EINVAL;
+    MSCD_CUDA(cudaSetDevice(c->device));
+    const bool dev = flags & MSCD_DEVICE_PTRS;
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaStream_t st = c->own;
+    i64 nnz = 0;
+    if (dev) MSCD_CUDA(cudaMemcpy(&nnz, row_ptr + n, sizeof(i64), cudaMemcpyDeviceToHost));
+    else nnz = row_ptr[n];
+    if (nnz < 0 || (nnz > 0 && !col)) return MSCD_EINVAL;
+    GraphRec g;
+    int rc = MSCD_OK;
+    do {
+        if ((rc = cuda_status(cudaMalloc((void **)&g.rp, (size_t)(n + 1) * sizeof(i64))))) break;
+        if ((rc = cuda_status(cudaMalloc((void **)&g.col, (size_t)std::max<i64>(nnz, 1) * sizeof(i32))))) break;
+        if ((rc = cuda_status(cudaMemcpyAsync(g.rp, row_ptr, (size_t)(n + 1) * sizeof(i64), kind, st)))) break;
+        if (nnz > 0 && (rc = cuda_status(cudaMemcpyAsync(g.col, col, (size_t)nnz * sizeof(i32), kind, st)))) break;
+        if (w) {
+            if ((rc = cuda_status(cudaMalloc((void **)&g.w, (size_t)std::max<i64>(nnz, 1) * sizeof(float))))) break;
+            if (nnz > 0 && (rc = cuda_status(cudaMemcpyAsync(g.w, w, (size_t)nnz * sizeof(float), kind, st)))) break;
+        }
+        rc = graph_prepare(n, g.rp, g.col, g.w, &g.g, &g.wfx, &g.k, &g.logk, st);
+    } while (0);
+    if (rc != MSCD_OK) {
+        cudaStreamSynchronize(st);
+        free_graph(g);
+        return rc;
+    }
+    cudaFree(g.w);  // the exact fixed-point copy replaces it
+    g.w = nullptr;
+    g.live = true;
+    int32_t id = -1;
+    for (size_t i = 0; i < c->graphs.size(); ++i)
+        if (!c->graphs[i].live) {
+            id = (int32_t)i;
+            break;
+        }
+    if (id < 0) {
+        id = (int32_t)c->graphs.size();
+        c->graphs.push_back(g);
+    } else {
+        c->graphs[id] = g;
+    }
+    *graph_id = id;
+    return MSCD_OK;
+}
+
+int mscd_graph_free(mscd_ctx *c, int32_t graph_id) {
+    GraphRec *g = find_graph(c, graph_id);
+    if (!g) return MSCD_EINVAL;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->own);
+    free_graph(*g);
+    return MSCD_OK;
+}
+
+int mscd_graph_info(mscd_ctx *c, int32_t graph_id, int64_t *n, int64_t *nnz, int32_t *unit_exp, int64_t *volume) {
+    GraphRec *g = find_graph(c, graph_id);
+    if (!g) return MSCD_EINVAL;
+    if (n) *n = g->g.n;
+    if (nnz) *nnz = g->g.nnz;
+    if (unit_exp) *unit_exp = g->g.unit_exp;
+    if (volume) *volume = g->g.volume;
+    return MSCD_OK;
+}
+
+int mscd_graph_degrees(mscd_ctx *c, int32_t graph_id, int64_t *k) {
+    GraphRec *g = find_graph(c, graph_id);
+    if (!g || !k) return MSCD_EINVAL;
+    MSCD_CUDA(cudaSetDevice(c->device));
+    if (g->g.n > 0) MSCD_CUDA(cudaMemcpy(k, g->g.k, (size_t)g->g.n * sizeof(i64), cudaMemcpyDeviceToHost));
+    return MSCD_OK;
+}
+
+int mscd_scales_logspaced(double vmin, double a, int32_t x, double *out) {
+    if (x < 1 || !out || !(vmin > 0.0) || !(a >= vmin) || !std::isfinite(a)) return MSCD_EINVAL;
+    if (x == 1) {
+        out[0] = a;
+        return MSCD_OK;
+    }
+    const double lx = std::log((double)x);
+    for (int32_t k = 1; k <= x; ++k) out[k - 1] = vmin + (a - vmin) * (1.0 - std::log((double)k) / lx);
+    return MSCD_OK;
+}
+
+int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scales, const int32_t *seeds,
+             int64_t n_seeds, uint32_t flags, void *cuda_stream) {
+    GraphRec *gr = find_graph(c, graph_id);
+    if (!gr || !alphas || n_scales < 1) return MSCD_EINVAL;
+    MSCD_CUDA(cudaSetDevice(c->device));
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c->own;
+    const bool dev = flags & MSCD_DEVICE_PTRS;
+    const DevGraph &G = gr->g;
+    const i64 N = seeds ? n_seeds : G.n;
+    if (N < 0) return MSCD_EINVAL;
+    std::vector<double> ha(n_scales);
+    if (dev) MSCD_CUDA(cudaMemcpy(ha.data(), alphas, n_scales * sizeof(double), cudaMemcpyDeviceToHost));
+    else std::memcpy(ha.data(), alphas, n_scales * sizeof(double));
+    for (double a : ha)
+        if (!(a > 0.0) || !std::isfinite(a)) return MSCD_EINVAL;
+    free_run(c);
+    c->stats = mscd_run_stats{};
+    c->S = n_scales;
+    c->N = N;
+    c->U = (i64)n_scales * N;
+    c->n_nodes_graph = G.n;
+    const i64 U = c->U;
+    cudaEvent_t ev[4];
+    for (auto &e : ev) cudaEventCreate(&e);
+    Counters *ctr = nullptr;
+    i64 *retry_a = nullptr, *retry_b = nullptr;
+    int rc = MSCD_OK;
+    cudaEventRecord(ev[0], st);
+    do {
+        if ((rc = cuda_status(cudaMalloc((void **)&c->alphas, n_scales * sizeof(double))))) break;
+        if ((rc = cuda_status(cudaMemcpyAsync(c->alphas, ha.data(), n_scales * sizeof(double), cudaMemcpyHostToDevice,
+                                              st))))
+            break;
+        if (seeds && N > 0) {
+            if ((rc = cuda_status(cudaMalloc((void **)&c->seeds, N * sizeof(i32))))) break;
+            if ((rc = cuda_status(cudaMemcpyAsync(c->seeds, seeds, N * sizeof(i32),
+                                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st))))
+                break;
+        }
+        const size_t U1 = (size_t)std::max<i64>(U, 1);
+        if ((rc = cuda_status(cudaMalloc((void **)&c->uoff, U1 * sizeof(i64))))) break;
+        if ((rc = cuda_status(cudaMalloc((void **)&c->ulen, U1 * sizeof(i32))))) break;
+        if ((rc = cuda_status(cudaMalloc((void **)&c->uhash, U1 * sizeof(u64))))) break;
+        if ((rc = cuda_status(cudaMalloc((void **)&c->uf, U1 * sizeof(double))))) break;
+        if ((rc = cuda_status(cudaMalloc((void **)&c->ustat, U1 * MSCD_NSTATS * sizeof(i64))))) break;
+        if ((rc = cuda_status(cudaMalloc((void **)&c->ustatus, U1 * sizeof(i32))))) break;
+        if ((rc = cuda_status(cudaMalloc((void **)&ctr, sizeof(Counters))))) break;
+        if ((rc = cuda_status(cudaMalloc((void **)&retry_a, U1 * sizeof(i64))))) break;
+        if ((rc = cuda_status(cudaMalloc((void **)&retry_b, U1 * sizeof(i64))))) break;
+        if ((rc = grow_output(c, std::max<i64>(U * 64, 1 << 20), st))) break;
+        if (c->seeds) {
+            if ((rc = cuda_status(cudaMemsetAsync(ctr, 0, sizeof(Counters), st)))) break;
+            check_seeds<<<152 * 8, 256, 0, st>>>(c->seeds, N, G.n, &ctr->error_flags);
+            u32 bad = 0;
+            if ((rc = cuda_status(cudaMemcpyAsync(&bad, &ctr->error_flags, sizeof(u32), cudaMemcpyDeviceToHost, st))))
+                break;
+            if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+            if (bad) { rc = MSCD_EINVAL; break; }
+        }
+        // ---- growth: a task list of (slot class, units) ----
+        std::vector<Task> tasks;
+        if (U > 0) tasks.push_back(Task{c->p.smem_slots, {}, true});
+        const int wpb = c->p.warps_per_block;
+        unsigned long long cursor = 0;
+        while (!tasks.empty() && rc == MSCD_OK) {
+            Task t = std::move(tasks.front());
+            tasks.erase(tasks.begin());
+            const i64 n_work = t.all ? U : (i64)t.units.size();
+            if ((rc = cuda_status(cudaMemsetAsync(ctr, 0, sizeof(Counters), st)))) break;
+            GrowArgs a{};
+            a.G = G;
+            a.alphas = c->alphas;
+            a.seeds = c->seeds;
+            a.n_seeds = N;
+            a.n_work = n_work;
+            a.work_counter = &ctr->work;
+            a.cap = t.cap;
+            a.max_rounds = c->p.max_rounds;
+            a.out_nodes = c->out_nodes;
+            a.out_cursor = &ctr->out_cursor;
+            a.out_needed = &ctr->out_needed;
+            a.out_cap = c->out_cap;
+            a.uoff = c->uoff;
+            a.ulen = c->ulen;
+            a.uhash = c->uhash;
+            a.uf = c->uf;
+            a.ustat = c->ustat;
+            a.ustatus = c->ustatus;
+            a.retry_state = retry_a;
+            a.n_retry_state = &ctr->n_retry_state;
+            a.retry_out = retry_b;
+            a.n_retry_out = &ctr->n_retry_out;
+            a.error_flags = &ctr->error_flags;
+            a.state_bytes = grow_state_bytes(t.cap);
+            i64 *list_dev = nullptr;
+            if (!t.all) {
+                if ((rc = cuda_status(cudaMallocAsync((void **)&list_dev, n_work * sizeof(i64), st)))) break;
+                if ((rc = cuda_status(cudaMemcpyAsync(list_dev, t.units.data(), n_work * sizeof(i64),
+                                                      cudaMemcpyHostToDevice, st))))
+                    break;
+                a.work_list = list_dev;
+            }
+            // unit lists are appended after everything earlier launches wrote
+            if ((rc = cuda_status(cudaMemcpyAsync(&ctr->out_cursor, &cursor, sizeof(cursor), cudaMemcpyHostToDevice,
+                                                  st))))
+                break;
+            const bool smem_class = t.cap == c->p.smem_slots;
+            int blocks = 0, threads = wpb * 32;
+            size_t smem = 0;
+            if (smem_class) {
+                a.use_smem = 1;
+                smem = (size_t)wpb * a.state_bytes;
+                int per_sm = 0;
+                if ((rc = grow_occupancy(threads, smem, &per_sm))) break;
+                if (c->p.blocks_per_sm > 0) per_sm = std::min(per_sm, c->p.blocks_per_sm);
+                if (per_sm < 1) { rc = MSCD_EINVAL; break; }
+                blocks = per_sm * c->sm_count;
+            } else {
+                a.use_smem = 0;
+                const size_t budget = (size_t)4 << 30;
+                i64 warps = std::max<i64>(1, std::min<i64>((i64)(budget / a.state_bytes), (i64)c->sm_count * 16));
+                warps = std::min<i64>(warps, std::max<i64>(n_work, 1));
+                threads = (int)std::min<i64>(warps, wpb) * 32;
+                blocks = (int)((warps + threads / 32 - 1) / (threads / 32));
+                if ((rc = ensure_arena(c, (size_t)blocks * (threads / 32) * a.state_bytes))) break;
+                a.gstate = c->arena;
+            }
+            blocks = (int)std::max<i64>(1, std::min<i64>(blocks, (n_work + threads / 32 - 1) / (threads / 32)));
+            if ((rc = grow_launch(a, blocks, threads, smem, st))) break;
+            c->stats.grow_launches++;
+            Counters h{};
+            if ((rc = cuda_status(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st)))) break;
+            if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+            if (list_dev) cudaFree(list_dev);
+            if (h.error_flags) { rc = MSCD_EDEVICE; break; }
+            if (!h.n_retry_out) {
+                cursor = h.out_cursor;
+            } else {
+                // Reservations are taken in increasing order and every list is
+                // non-empty, so once one fails all later ones fail: every
+                // written list lies below the old capacity.
+                std::vector<i64> lst(h.n_retry_out);
+                if ((rc = cuda_status(cudaMemcpy(lst.data(), retry_b, lst.size() * sizeof(i64),
+                                                 cudaMemcpyDeviceToHost))))
+                    break;
+                cursor = (unsigned long long)c->out_cap;
+                if ((rc = grow_output(c, c->out_cap + (i64)h.out_needed + (1 << 20), st))) break;
+                tasks.insert(tasks.begin(), Task{t.cap, std::move(lst), false});
+            }
+            if (h.n_retry_state) {
+                std::vector<i64> lst(h.n_retry_state);
+                if ((rc = cuda_status(cudaMemcpy(lst.data(), retry_a, lst.size() * sizeof(i64),
+                                                 cudaMemcpyDeviceToHost))))
+                    break;
+                c->stats.overflow_units += (i64)lst.size();
+                i64 next = (i64)t.cap * 8;
+                i64 full = 32;
+                while (full < G.n + 1) full <<= 1;
+                next = std::min(next, full);
+                if (next <= t.cap) { rc = MSCD_EDEVICE; break; }
+                tasks.push_back(Task{(int)next, std::move(lst), false});
+            }
+        }
+        if (rc) break;
+        cudaEventRecord(ev[1], st);
+        // ---- totals ----
+        unsigned long long *tot = nullptr;
+        if ((rc = cuda_status(cudaMallocAsync((void **)&tot, 8 * sizeof(unsigned long long), st)))) break;
+        cudaMemsetAsync(tot, 0, 8 * sizeof(unsigned long long), st);
+        if (U > 0) sum_unit_stats<<<152 * 4, 256, 0, st>>>(c->ustat, c->ulen, c->ustatus, U, tot);
+        unsigned long long ht[8];
+        cudaMemcpyAsync(ht, tot, sizeof(ht), cudaMemcpyDeviceToHost, st);
+        cudaFreeAsync(tot, st);
+        if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+        c->stats.units = U;
+        c->stats.edges_scanned = (i64)ht[0];
+        c->stats.adds = (i64)ht[1];
+        c->stats.removes = (i64)ht[2];
+        c->stats.slow_decisions = (i64)ht[3];
+        c->stats.undecided = (i64)ht[4];
+        c->stats.member_entries = (i64)ht[7];
+        const i64 n_timeout = (i64)ht[5], n_undecided = (i64)ht[6];
+        // ---- dedup per scale ----
+        c->scales.resize(n_scales);
+        for (int32_t s = 0; s < n_scales && rc == MSCD_OK; ++s)
+            rc = dedup_scale(c->uoff + s * N, c->ulen + s * N, c->uhash + s * N, c->uf + s * N, c->out_nodes, N,
+                             &c->scales[s], st);
+        if (rc) break;
+        cudaEventRecord(ev[2], st);
+        // ---- stability ----
+        c->nmi_succ.assign(std::max(n_scales - 1, 0), NAN);
+        for (int32_t s = 0; s + 1 < n_scales && rc == MSCD_OK; ++s)
+            rc = nmi_between(c->scales[s], c->scales[s + 1], G.n, &c->nmi_succ[s], st);
+        if (rc) break;
+        window_means(c->nmi_succ, n_scales, 3, c->win3);
+        window_means(c->nmi_succ, n_scales, 5, c->win5);
+        cudaEventRecord(ev[3], st);
+        if ((rc = cuda_status(cudaEventSynchronize(ev[3])))) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        c->stats.ms_grow = ms;
+        cudaEventElapsedTime(&ms, ev[1], ev[2]);
+        c->stats.ms_dedup = ms;
+        cudaEventElapsedTime(&ms, ev[2], ev[3]);
+        c->stats.ms_stability = ms;
+        cudaEventElapsedTime(&ms, ev[0], ev[3]);
+        c->stats.ms_total = ms;
+        c->have = true;
+        if (n_undecided) rc = MSCD_EUNDECIDED;
+        else if (n_timeout) rc = MSCD_ETIMEOUT;
+    } while (0);
+    cudaStreamSynchronize(st);
+    cudaFree(ctr);
+    cudaFree(retry_a);
+    cudaFree(retry_b);
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (rc != MSCD_OK && !c->have) free_run(c);
+    return rc;
+}
+
+int mscd_get_membership(mscd_ctx *c, int32_t scale_idx, int64_t seed_idx, int32_t *buf, int64_t cap, int64_t *len,
+                        double *fitness) {
+    if (!c || !len) return MSCD_EINVAL;
+    if (!c->have) return MSCD_ENORESULT;
+    if (scale_idx < 0 || scale_idx >= c->S || seed_idx < 0 || seed_idx >= c->N) return MSCD_EINVAL;
+    MSCD_CUDA(cudaSetDevice(c->device));
+    const i64 u = (i64)scale_idx * c->N + seed_idx;
+    i64 off = 0;
+    i32 m = 0;
+    MSCD_CUDA(cudaMemcpy(&off, c->uoff + u, sizeof(i64), cudaMemcpyDeviceToHost));
+    MSCD_CUDA(cudaMemcpy(&m, c->ulen + u, sizeof(i32), cudaMemcpyDeviceToHost));
+    if (fitness) MSCD_CUDA(cudaMemcpy(fitness, c->uf + u, sizeof(double), cudaMemcpyDeviceToHost));
+    *len = m;
+    if (cap < m || (m > 0 && !buf)) return MSCD_ESMALL;
+    if (m > 0) MSCD_CUDA(cudaMemcpy(buf, c->out_nodes + off, (size_t)m * sizeof(i32), cudaMemcpyDeviceToHost));
+    return MSCD_OK;
+}
+
+int mscd_get_memberships(mscd_ctx *c, int32_t scale_idx, int64_t *ptr, int32_t *nodes, int64_t nodes_cap,
+                         double *fitness, int64_t *stats, int64_t *n_nodes) {
+    if (!c || !n_nodes) return MSCD_EINVAL;
+    if (!c->have) return MSCD_ENORESULT;
+    if (scale_idx < 0 || scale_idx >= c->S) return MSCD_EINVAL;
+    MSCD_CUDA(cudaSetDevice(c->device));
+    cudaStream_t st = c->own;
+    const i64 N = c->N, base = (i64)scale_idx * N;
+    i64 *dptr = nullptr;
+    i32 *dnodes = nullptr;
+    int rc = MSCD_OK;
+    do {
+        if ((rc = cuda_status(cudaMallocAsync((void **)&dptr, (N + 1) * sizeof(i64), st)))) break;
+        if (N > 0) widen_len<<<152 * 4, 256, 0, st>>>(c->ulen + base, N, dptr);
+        if ((rc = scan_exclusive_i64(dptr, dptr, N, dptr + N, st))) break;
+        i64 total = 0;
+        if ((rc = cuda_status(cudaMemcpyAsync(&total, dptr + N, sizeof(i64), cudaMemcpyDeviceToHost, st)))) break;
+        if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+        *n_nodes = total;
+        if (ptr && (rc = cuda_status(cudaMemcpy(ptr, dptr, (N + 1) * sizeof(i64), cudaMemcpyDeviceToHost)))) break;
+        if (fitness && N > 0 &&
+            (rc = cuda_status(cudaMemcpy(fitness, c->uf + base, N * sizeof(double), cudaMemcpyDeviceToHost))))
+            break;
+        if (stats && N > 0 &&
+            (rc = cuda_status(cudaMemcpy(stats, c->ustat + base * MSCD_NSTATS, N * MSCD_NSTATS * sizeof(i64),
+                                         cudaMemcpyDeviceToHost))))
+            break;
+        if (nodes_cap < total || (total > 0 && !nodes)) { rc = MSCD_ESMALL; break; }
+        if (total > 0) {
+            if ((rc = cuda_status(cudaMallocAsync((void **)&dnodes, total * sizeof(i32), st)))) break;
+            gather_lists<<<152 * 8, 256, 0, st>>>(c->uoff + base, c->ulen + base, dptr, c->out_nodes, N, dnodes);
+            if ((rc = cuda_status(cudaMemcpyAsync(nodes, dnodes, total * sizeof(i32), cudaMemcpyDeviceToHost, st))))
+                break;
+        }
+        rc = cuda_status(cudaStreamSynchronize(st));
+    } while (0);
+    cudaFreeAsync(dptr, st);
+    if (dnodes) cudaFreeAsync(dnodes, st);
+    cudaStreamSynchronize(st);
+    return rc;
+}
+
+int mscd_get_communities(mscd_ctx *c, int32_t scale_idx, int64_t *ptr, int64_t ptr_cap, int32_t *nodes,
+                         int64_t nodes_cap, double *fitness, int32_t *seed2comm, int64_t *n_comms, int64_t *n_nodes) {
+    if (!c || !n_comms || !n_nodes) return MSCD_EINVAL;
+    if (!c->have) return MSCD_ENORESULT;
+    if (scale_idx < 0 || scale_idx >= c->S) return MSCD_EINVAL;
+    MSCD_CUDA(cudaSetDevice(c->device));
+    const ScaleResult &r = c->scales[scale_idx];
+    *n_comms = r.n_comms;
+    *n_nodes = r.n_nodes;
+    if (seed2comm && c->N > 0)
+        MSCD_CUDA(cudaMemcpy(seed2comm, r.seed2comm, c->N * sizeof(i32), cudaMemcpyDeviceToHost));
+    if (fitness && r.n_comms > 0)
+        MSCD_CUDA(cudaMemcpy(fitness, r.comm_f, r.n_comms * sizeof(double), cudaMemcpyDeviceToHost));
+    if (ptr_cap < r.n_comms + 1 || nodes_cap < r.n_nodes || !ptr || (r.n_nodes > 0 && !nodes)) return MSCD_ESMALL;
+    MSCD_CUDA(cudaMemcpy(ptr, r.comm_ptr, (r.n_comms + 1) * sizeof(i64), cudaMemcpyDeviceToHost));
+    if (r.n_nodes > 0) MSCD_CUDA(cudaMemcpy(nodes, r.comm_nodes, r.n_nodes * sizeof(i32), cudaMemcpyDeviceToHost));
+    return MSCD_OK;
+}
+
+int mscd_get_stability(mscd_ctx *c, double *nmi_succ, double *nmi_win3, double *nmi_win5) {
+    if (!c) return MSCD_EINVAL;
+    if (!c->have) return MSCD_ENORESULT;
+    if (nmi_succ) std::copy(c->nmi_succ.begin(), c->nmi_succ.end(), nmi_succ);
+    if (nmi_win3) std::copy(c->win3.begin(), c->win3.end(), nmi_win3);
+    if (nmi_win5) std::copy(c->win5.begin(), c->win5.end(), nmi_win5);
+    return MSCD_OK;
+}
+
+int mscd_get_run_stats(mscd_ctx *c, mscd_run_stats *out) {
+    if (!c || !out) return MSCD_EINVAL;
+    if (!c->have) return MSCD_ENORESULT;
+    *out = c->stats;
+    return MSCD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,202 @@
+// Deduplication of the communities of one scale.
+//
+// Communities grown from different seeds are the same community iff their
+// sorted member lists are equal (the paper keeps community nodes sorted,
+// Sec. 3).  Units are grouped by the 64-bit hash of their list in a device
+// hash table; the representative of a group is its smallest unit (= seed)
+// index; every unit's list is compared element by element with its
+// representative's, and the rare unit whose list differs despite an equal
+// hash is regrouped exactly by a plain pairwise pass.  Unique communities are
+// numbered in order of their representative (smallest generating seed index).
+#include <algorithm>
+
+#include "common.cuh"
+#include "dedup.cuh"
+
+namespace {
+
+__global__ void table_insert(const u64 *uhash, i64 N, u64 *tkey, i64 *trep, i64 tmask, i64 *uent, u32 *err) {
+    for (i64 u = (i64)blockIdx.x * blockDim.x + threadIdx.x; u < N; u += (i64)gridDim.x * blockDim.x) {
+        const u64 key = uhash[u];
+        i64 h = (i64)(key & (u64)tmask);
+        i64 p = 0;
+        for (; p <= tmask; ++p) {
+            const u64 old = atomicCAS((unsigned long long *)&tkey[h], 0ull, (unsigned long long)key);
+            if (old == 0ull || old == key) break;
+            h = (h + 1) & tmask;
+        }
+        if (p > tmask) {
+            atomicOr(err, 1u);
+            h = 0;
+        }
+        uent[u] = h;
+        atomicMin((long long *)&trep[h], (long long)u);
+    }
+}
+
+// Warp per unit: compare the list with the representative's.
+__global__ void verify(const i64 *uoff, const i32 *ulen, const i32 *nodes, const i64 *uent, const i64 *trep, i64 N,
+                       i64 *urep, unsigned long long *n_coll) {
+    const int lane = threadIdx.x & 31;
+    const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
+    for (i64 u = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < N; u += warps) {
+        const i64 r = trep[uent[u]];
+        bool same = true;
+        if (r != u) {
+            same = ulen[u] == ulen[r];
+            if (same) {
+                const i32 *a = nodes + uoff[u], *b = nodes + uoff[r];
+                const int m = ulen[u];
+                bool diff = false;
+                for (int i = lane; i < m; i += 32) diff |= a[i] != b[i];
+                same = !__any_sync(FULL_MASK, diff);
+            }
+        }
+        if (lane == 0) {
+            urep[u] = same ? r : -1;
+            if (!same) atomicAdd(n_coll, 1ull);
+        }
+    }
+}
+
+// Plain pairwise regrouping of the units whose list differed from their
+// hash group's representative (equal lists have equal hashes, so every such
+// group lies entirely inside this set).  Single thread; expected never to run.
+__global__ void regroup_collisions(const i64 *uoff, const i32 *ulen, const i32 *nodes, i64 N, i64 *urep) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (i64 u = 0; u < N; ++u) {
+        if (urep[u] != -1) continue;
+        urep[u] = u;
+        for (i64 v = 0; v < u; ++v) {
+            if (urep[v] != v || ulen[v] != ulen[u]) continue;
+            // v is a regrouped representative only if it was itself a collision
+            const i32 *a = nodes + uoff[u], *b = nodes + uoff[v];
+            bool eq = true;
+            for (int i = 0; i < ulen[u] && eq; ++i) eq = a[i] == b[i];
+            if (eq) {
+                urep[u] = v;
+                break;
+            }
+        }
+    }
+}
+
+__global__ void mark_reps(const i64 *urep, i64 N, i64 *flag) {
+    for (i64 u = (i64)blockIdx.x * blockDim.x + threadIdx.x; u < N; u += (i64)gridDim.x * blockDim.x)
+        flag[u] = urep[u] == u ? 1 : 0;
+}
+
+__global__ void fill_comms(const i64 *urep, const i64 *cid, const i32 *ulen, const double *uf, i64 N, i64 *clen,
+                           double *cf, i64 *crep, i32 *seed2comm) {
+    for (i64 u = (i64)blockIdx.x * blockDim.x + threadIdx.x; u < N; u += (i64)gridDim.x * blockDim.x) {
+        const i64 r = urep[u];
+        seed2comm[u] = (i32)cid[r];
+        if (r == u) {
+            const i64 c = cid[u];
+            clen[c] = ulen[u];
+            cf[c] = uf[u];
+            crep[c] = u;
+        }
+    }
+}
+
+__global__ void copy_lists(const i64 *crep, const i64 *cptr, const i64 *uoff, const i32 *nodes, i64 C, i32 *cnodes) {
+    const int lane = threadIdx.x & 31;
+    const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
+    for (i64 c = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < C; c += warps) {
+        const i32 *src = nodes + uoff[crep[c]];
+        i32 *dst = cnodes + cptr[c];
+        const i64 m = cptr[c + 1] - cptr[c];
+        for (i64 i = lane; i < m; i += 32) dst[i] = src[i];
+    }
+}
+
+}  // namespace
+
+void scale_result_free(ScaleResult *r) {
+    cudaFree(r->comm_ptr);
+    cudaFree(r->comm_nodes);
+    cudaFree(r->comm_f);
+    cudaFree(r->seed2comm);
+    *r = ScaleResult{};
+}
+
+int dedup_scale(const i64 *uoff, const i32 *ulen, const u64 *uhash, const double *uf, const i32 *nodes, i64 N,
+                ScaleResult *out, cudaStream_t st) {
+    *out = ScaleResult{};
+    if (N <= 0) {
+        MSCD_CUDA(cudaMalloc((void **)&out->comm_ptr, sizeof(i64)));
+        MSCD_CUDA(cudaMemsetAsync(out->comm_ptr, 0, sizeof(i64), st));
+        return MSCD_OK;
+    }
+    i64 T = 1;
+    while (T < 2 * N) T <<= 1;
+    u64 *tkey = nullptr;
+    i64 *trep = nullptr, *uent = nullptr, *urep = nullptr, *flag = nullptr, *cid = nullptr, *clen = nullptr,
+        *crep = nullptr, *tot = nullptr;
+    unsigned long long *ncoll = nullptr;
+    u32 *err = nullptr;
+    int rc = MSCD_OK;
+    const unsigned blocks = (unsigned)std::min<i64>((N + 255) / 256, 152 * 16);
+    const unsigned wblocks = (unsigned)std::min<i64>((N + 7) / 8, 152 * 16);
+    do {
+        if ((rc = cuda_status(cudaMallocAsync((void **)&tkey, T * sizeof(u64), st)))) break;
+        if ((rc = cuda_status(cudaMallocAsync((void **)&trep, T * sizeof(i64), st)))) break;
+        if ((rc = cuda_status(cudaMallocAsync((void **)&uent, N * sizeof(i64), st)))) break;
+        if ((rc = cuda_status(cudaMallocAsync((void **)&urep, N * sizeof(i64), st)))) break;
+        if ((rc = cuda_status(cudaMallocAsync((void **)&flag, (N + 1) * sizeof(i64), st)))) break;
+        if ((rc = cuda_status(cudaMallocAsync((void **)&cid, (N + 1) * sizeof(i64), st)))) break;
+        if ((rc = cuda_status(cudaMallocAsync((void **)&tot, 2 * sizeof(i64) + 2 * sizeof(unsigned long long), st))))
+            break;
+        ncoll = (unsigned long long *)(tot + 1);
+        err = (u32 *)(tot + 2);
+        if ((rc = cuda_status(cudaMemsetAsync(tkey, 0, T * sizeof(u64), st)))) break;
+        if ((rc = cuda_status(cudaMemsetAsync(trep, 0x7f, T * sizeof(i64), st)))) break;
+        if ((rc = cuda_status(cudaMemsetAsync(tot, 0, 2 * sizeof(i64) + 2 * sizeof(unsigned long long), st)))) break;
+        table_insert<<<blocks, 256, 0, st>>>(uhash, N, tkey, trep, T - 1, uent, err);
+        verify<<<wblocks, 256, 0, st>>>(uoff, ulen, nodes, uent, trep, N, urep, ncoll);
+        unsigned long long h_coll = 0;
+        u32 h_err = 0;
+        if ((rc = cuda_status(cudaMemcpyAsync(&h_coll, ncoll, sizeof(h_coll), cudaMemcpyDeviceToHost, st)))) break;
+        if ((rc = cuda_status(cudaMemcpyAsync(&h_err, err, sizeof(h_err), cudaMemcpyDeviceToHost, st)))) break;
+        if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+        if (h_err) { rc = MSCD_EDEVICE; break; }
+        if (h_coll) regroup_collisions<<<1, 32, 0, st>>>(uoff, ulen, nodes, N, urep);
+        mark_reps<<<blocks, 256, 0, st>>>(urep, N, flag);
+        if ((rc = scan_exclusive_i64(flag, cid, N, tot, st))) break;
+        i64 C = 0;
+        if ((rc = cuda_status(cudaMemcpyAsync(&C, tot, sizeof(i64), cudaMemcpyDeviceToHost, st)))) break;
+        if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+        out->n_comms = C;
+        if ((rc = cuda_status(cudaMallocAsync((void **)&clen, (C + 1) * sizeof(i64), st)))) break;
+        if ((rc = cuda_status(cudaMallocAsync((void **)&crep, (C + 1) * sizeof(i64), st)))) break;
+        if ((rc = cuda_status(cudaMalloc((void **)&out->comm_ptr, (C + 1) * sizeof(i64))))) break;
+        if ((rc = cuda_status(cudaMalloc((void **)&out->comm_f, std::max<i64>(C, 1) * sizeof(double))))) break;
+        if ((rc = cuda_status(cudaMalloc((void **)&out->seed2comm, N * sizeof(i32))))) break;
+        fill_comms<<<blocks, 256, 0, st>>>(urep, cid, ulen, uf, N, clen, out->comm_f, crep, out->seed2comm);
+        if ((rc = scan_exclusive_i64(clen, out->comm_ptr, C, out->comm_ptr + C, st))) break;
+        i64 total = 0;
+        if ((rc = cuda_status(cudaMemcpyAsync(&total, out->comm_ptr + C, sizeof(i64), cudaMemcpyDeviceToHost, st))))
+            break;
+        if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+        out->n_nodes = total;
+        if ((rc = cuda_status(cudaMalloc((void **)&out->comm_nodes, std::max<i64>(total, 1) * sizeof(i32))))) break;
+        const unsigned cblocks = (unsigned)std::max<i64>(1, std::min<i64>((C + 7) / 8, 152 * 16));
+        if (C > 0) copy_lists<<<cblocks, 256, 0, st>>>(crep, out->comm_ptr, uoff, nodes, C, out->comm_nodes);
+        rc = cuda_status(cudaGetLastError());
+    } while (0);
+    cudaFreeAsync(tkey, st);
+    cudaFreeAsync(trep, st);
+    cudaFreeAsync(uent, st);
+    cudaFreeAsync(urep, st);
+    cudaFreeAsync(flag, st);
+    cudaFreeAsync(cid, st);
+    cudaFreeAsync(clen, st);
+    cudaFreeAsync(crep, st);
+    cudaFreeAsync(tot, st);
+    if (rc != MSCD_OK) {
+        cudaStreamSynchronize(st);
+        scale_result_free(out);
+    }
+    return rc;
+}

@@ -1,0 +1,44 @@
+// Launch interface of the growth kernel.
+#pragma once
+
+#include "common.cuh"
+
+#define GROW_MAX_THREADS 512
+
+struct GrowArgs {
+    DevGraph G;
+    const double *alphas;   // [n_scales]
+    const i32 *seeds;       // [n_seeds] or null = node ids 0..n_seeds-1
+    i64 n_seeds;
+    // work: units 0..n_work-1, or the listed units
+    const i64 *work_list;
+    i64 n_work;
+    unsigned long long *work_counter;
+    // per-warp node-slot state
+    int cap;                // slots per warp (power of 2)
+    int use_smem;           // 1: dynamic shared memory, 0: global arena
+    unsigned char *gstate;  // global arena (warps * state_bytes)
+    size_t state_bytes;
+    i64 max_rounds;
+    // outputs (unit-indexed)
+    i32 *out_nodes;
+    unsigned long long *out_cursor;
+    unsigned long long *out_needed;
+    i64 out_cap;
+    i64 *uoff;
+    i32 *ulen;
+    u64 *uhash;
+    double *uf;
+    i64 *ustat;
+    i32 *ustatus;
+    // units to grow again: slot capacity exceeded / output buffer full
+    i64 *retry_state;
+    unsigned long long *n_retry_state;
+    i64 *retry_out;
+    unsigned long long *n_retry_out;
+    u32 *error_flags;
+};
+
+size_t grow_state_bytes(int cap);
+int grow_launch(const GrowArgs &a, int blocks, int threads, size_t smem, cudaStream_t st);
+int grow_occupancy(int threads, size_t smem, int *blocks_per_sm);

@@ -1,0 +1,253 @@
+"""Thin Python binding of libmscd.so (include/mscd.h): argument marshalling only.
+
+Every function of the C ABI is exposed under its C name; ``Context`` wraps a
+context with numpy / torch friendly helpers.  Arrays may be numpy arrays
+(host) or CUDA torch tensors (device, passed with MSCD_DEVICE_PTRS).  There
+is no fallback: if the library cannot be loaded, import fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libmscd.so")
+
+OK = 0
+EINVAL, ENOTSYM, ESELFLOOP, EDUP, ERANGE, ENOMEM, EDEVICE = -1, -2, -3, -4, -5, -6, -7
+ETIMEOUT, ESMALL, EUNDECIDED, EUNSORTED, EWEIGHT, ENORESULT = -8, -9, -10, -11, -12, -13
+DEVICE_PTRS = 1
+NSTATS = 8
+STAT_FIELDS = ("edges_scanned", "adds", "removes", "rounds", "K", "V", "slow", "undecided")
+
+i64p = C.POINTER(C.c_int64)
+i32p = C.POINTER(C.c_int32)
+f64p = C.POINTER(C.c_double)
+f32p = C.POINTER(C.c_float)
+vp = C.c_void_p
+
+
+class mscd_params(C.Structure):
+    _fields_ = [("struct_size", C.c_int32), ("warps_per_block", C.c_int32), ("smem_slots", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("max_rounds", C.c_int64)]
+
+
+class mscd_run_stats(C.Structure):
+    _fields_ = [("units", C.c_int64), ("edges_scanned", C.c_int64), ("adds", C.c_int64), ("removes", C.c_int64),
+                ("slow_decisions", C.c_int64), ("undecided", C.c_int64), ("overflow_units", C.c_int64),
+                ("grow_launches", C.c_int64), ("member_entries", C.c_int64), ("ms_grow", C.c_double),
+                ("ms_dedup", C.c_double), ("ms_stability", C.c_double), ("ms_total", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "mscd_strerror": (C.c_char_p, [C.c_int]),
+    "mscd_version": (C.c_int, []),
+    "mscd_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(mscd_params)]),
+    "mscd_destroy": (C.c_int, [vp]),
+    "mscd_graph_load_csr": (C.c_int, [vp, C.c_int64, vp, vp, vp, C.c_uint32, i32p]),
+    "mscd_graph_free": (C.c_int, [vp, C.c_int32]),
+    "mscd_graph_info": (C.c_int, [vp, C.c_int32, i64p, i64p, i32p, i64p]),
+    "mscd_graph_degrees": (C.c_int, [vp, C.c_int32, i64p]),
+    "mscd_scales_logspaced": (C.c_int, [C.c_double, C.c_double, C.c_int32, f64p]),
+    "mscd_run": (C.c_int, [vp, C.c_int32, vp, C.c_int32, vp, C.c_int64, C.c_uint32, vp]),
+    "mscd_get_membership": (C.c_int, [vp, C.c_int32, C.c_int64, i32p, C.c_int64, i64p, f64p]),
+    "mscd_get_memberships": (C.c_int, [vp, C.c_int32, i64p, i32p, C.c_int64, f64p, i64p, i64p]),
+    "mscd_get_communities": (C.c_int, [vp, C.c_int32, i64p, C.c_int64, i32p, C.c_int64, f64p, i32p, i64p, i64p]),
+    "mscd_get_stability": (C.c_int, [vp, f64p, f64p, f64p]),
+    "mscd_get_run_stats": (C.c_int, [vp, C.POINTER(mscd_run_stats)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (built by ``build.py``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError("libmscd.so not built: run paper_1301_0955_gb300/build.py (%s)" % path)
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(rc: int) -> str:
+    return load().mscd_strerror(rc).decode()
+
+
+class MscdError(RuntimeError):
+    def __init__(self, rc, what=""):
+        super().__init__("%s: %s (%d)" % (what, strerror(rc), rc))
+        self.rc = rc
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise MscdError(rc, what)
+    return rc
+
+
+def _ptr(a):
+    """(address, is_device) of a numpy array or torch tensor; None -> (None, False)."""
+    if a is None:
+        return None, False
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data, False
+    # torch tensor
+    assert a.is_contiguous()
+    return a.data_ptr(), bool(a.is_cuda)
+
+
+def scales_logspaced(vmin: float, a: float, x: int) -> np.ndarray:
+    out = np.zeros(max(x, 1), np.float64)
+    _check(load().mscd_scales_logspaced(vmin, a, x, out.ctypes.data_as(f64p)), "mscd_scales_logspaced")
+    return out
+
+
+class Context:
+    """One mscd context on one device."""
+
+    def __init__(self, device: int = 0, warps_per_block: int = 0, smem_slots: int = 0, blocks_per_sm: int = 0,
+                 max_rounds: int = 0):
+        L = load()
+        p = mscd_params(C.sizeof(mscd_params), warps_per_block, smem_slots, blocks_per_sm, max_rounds)
+        h = vp()
+        _check(L.mscd_create(C.byref(h), device, C.byref(p)), "mscd_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().mscd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- graphs
+    def load_csr(self, n, row_ptr, col, w=None) -> int:
+        """Returns the graph id; raises MscdError with the check's status code."""
+        rp, dev = _ptr(row_ptr)
+        cp, dev2 = _ptr(col)
+        wp, dev3 = _ptr(w)
+        assert dev == dev2 and (w is None or dev3 == dev)
+        gid = C.c_int32(-1)
+        rc = load().mscd_graph_load_csr(self.h, int(n), rp, cp, wp, DEVICE_PTRS if dev else 0, C.byref(gid))
+        _check(rc, "mscd_graph_load_csr")
+        return gid.value
+
+    def try_load_csr(self, n, row_ptr, col, w=None):
+        """(status, graph id or -1) without raising."""
+        try:
+            return OK, self.load_csr(n, row_ptr, col, w)
+        except MscdError as e:
+            return e.rc, -1
+
+    def free_graph(self, gid: int):
+        _check(load().mscd_graph_free(self.h, gid), "mscd_graph_free")
+
+    def graph_info(self, gid: int) -> dict:
+        n, nnz, vol = C.c_int64(), C.c_int64(), C.c_int64()
+        ue = C.c_int32()
+        _check(load().mscd_graph_info(self.h, gid, C.byref(n), C.byref(nnz), C.byref(ue), C.byref(vol)),
+               "mscd_graph_info")
+        return dict(n=n.value, nnz=nnz.value, unit_exp=ue.value, volume=vol.value)
+
+    def graph_degrees(self, gid: int) -> np.ndarray:
+        n = self.graph_info(gid)["n"]
+        k = np.zeros(max(n, 1), np.int64)
+        _check(load().mscd_graph_degrees(self.h, gid, k.ctypes.data_as(i64p)), "mscd_graph_degrees")
+        return k[:n]
+
+    # ---- run
+    def run(self, gid: int, alphas, seeds=None, stream=None) -> int:
+        """Returns the status (OK, ETIMEOUT or EUNDECIDED); raises on other errors."""
+        if isinstance(alphas, (list, tuple)):
+            alphas = np.asarray(alphas, np.float64)
+        ap, dev = _ptr(alphas)
+        n_scales = int(alphas.shape[0])
+        sp, sdev = _ptr(seeds)
+        n_seeds = 0 if seeds is None else int(seeds.shape[0])
+        if seeds is not None:
+            assert sdev == dev, "alphas and seeds must both be host or both be device arrays"
+        st = None
+        if stream is not None:
+            st = stream if isinstance(stream, int) else stream.cuda_stream
+        rc = load().mscd_run(self.h, gid, ap, n_scales, sp, n_seeds, DEVICE_PTRS if dev else 0, st)
+        if rc not in (OK, ETIMEOUT, EUNDECIDED):
+            raise MscdError(rc, "mscd_run")
+        self.n_scales = n_scales
+        self.n_seeds = n_seeds if seeds is not None else self.graph_info(gid)["n"]
+        return rc
+
+    def membership(self, scale: int, seed_idx: int):
+        ln = C.c_int64()
+        f = C.c_double()
+        rc = load().mscd_get_membership(self.h, scale, seed_idx, None, 0, C.byref(ln), C.byref(f))
+        if rc not in (OK, ESMALL):
+            raise MscdError(rc, "mscd_get_membership")
+        buf = np.zeros(max(ln.value, 1), np.int32)
+        _check(load().mscd_get_membership(self.h, scale, seed_idx, buf.ctypes.data_as(i32p), ln.value, C.byref(ln),
+                                          C.byref(f)), "mscd_get_membership")
+        return buf[: ln.value], f.value
+
+    def memberships(self, scale: int, with_stats: bool = True):
+        """(ptr[n_seeds+1], nodes, fitness[n_seeds], stats[n_seeds, 8])."""
+        N = self.n_seeds
+        ptr = np.zeros(N + 1, np.int64)
+        f = np.zeros(max(N, 1), np.float64)
+        stt = np.zeros((max(N, 1), NSTATS), np.int64)
+        tot = C.c_int64()
+        rc = load().mscd_get_memberships(self.h, scale, ptr.ctypes.data_as(i64p), None, 0, None, None, C.byref(tot))
+        if rc not in (OK, ESMALL):
+            raise MscdError(rc, "mscd_get_memberships")
+        nodes = np.zeros(max(tot.value, 1), np.int32)
+        _check(load().mscd_get_memberships(self.h, scale, ptr.ctypes.data_as(i64p), nodes.ctypes.data_as(i32p),
+                                           tot.value, f.ctypes.data_as(f64p),
+                                           stt.ctypes.data_as(i64p) if with_stats else None, C.byref(tot)),
+               "mscd_get_memberships")
+        return ptr, nodes[: tot.value], f[:N], stt[:N]
+
+    def communities(self, scale: int):
+        """(comm_ptr, comm_nodes, fitness, seed2comm)."""
+        nc, nn = C.c_int64(), C.c_int64()
+        rc = load().mscd_get_communities(self.h, scale, None, 0, None, 0, None, None, C.byref(nc), C.byref(nn))
+        if rc not in (OK, ESMALL):
+            raise MscdError(rc, "mscd_get_communities")
+        ptr = np.zeros(nc.value + 1, np.int64)
+        nodes = np.zeros(max(nn.value, 1), np.int32)
+        f = np.zeros(max(nc.value, 1), np.float64)
+        s2c = np.zeros(max(self.n_seeds, 1), np.int32)
+        _check(load().mscd_get_communities(self.h, scale, ptr.ctypes.data_as(i64p), nc.value + 1,
+                                           nodes.ctypes.data_as(i32p), nn.value, f.ctypes.data_as(f64p),
+                                           s2c.ctypes.data_as(i32p), C.byref(nc), C.byref(nn)),
+               "mscd_get_communities")
+        return ptr, nodes[: nn.value], f[: nc.value], s2c[: self.n_seeds]
+
+    def stability(self):
+        S = self.n_scales
+        a = np.zeros(max(S - 1, 1), np.float64)
+        b = np.zeros(S, np.float64)
+        c = np.zeros(S, np.float64)
+        _check(load().mscd_get_stability(self.h, a.ctypes.data_as(f64p), b.ctypes.data_as(f64p),
+                                         c.ctypes.data_as(f64p)), "mscd_get_stability")
+        return a[: S - 1], b, c
+
+    def run_stats(self) -> dict:
+        s = mscd_run_stats()
+        _check(load().mscd_get_run_stats(self.h, C.byref(s)), "mscd_get_run_stats")
+        return s.as_dict()
