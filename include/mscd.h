@@ -77,11 +77,15 @@ typedef struct mscd_ctx mscd_ctx;
 
 /* Tuning and limits.  Zero fields take the defaults. */
 typedef struct mscd_params {
-    int32_t struct_size;     /* sizeof(mscd_params)                                  */
-    int32_t warps_per_block; /* growth kernel: warps per CTA, one unit per warp (8)   */
-    int32_t smem_slots;      /* node slots per warp in shared memory (512, power of 2) */
-    int32_t blocks_per_sm;   /* persistent growth grid: CTAs per SM (from occupancy)   */
-    int64_t max_rounds;      /* grow/prune repetitions per unit before ETIMEOUT (1e6)  */
+    int32_t struct_size;     /* sizeof(mscd_params)                                     */
+    int32_t warps_per_block; /* global-arena classes: warps (units) per CTA (8)          */
+    int32_t smem_slots;      /* node slots of the first shared-memory class (power of 2
+                                >= 32; 0 = 1024, or 512 when weighted slots do not fit) */
+    int32_t blocks_per_sm;   /* first class: CTAs per SM (0 = from occupancy)           */
+    int32_t mid_slots;       /* node slots of an optional second shared-memory class
+                                (power of 2 >= 32; 0 = none)                            */
+    int32_t global_warps_per_sm; /* global-arena classes: resident units per SM (16)     */
+    int64_t max_rounds;      /* grow/prune repetitions per unit before ETIMEOUT (1e6)     */
 } mscd_params;
 
 /* Totals of the last run. */
@@ -95,6 +99,11 @@ typedef struct mscd_run_stats {
     int64_t grow_launches;    /* growth kernel launches                            */
     int64_t member_entries;   /* total member-list length over all units           */
     double ms_grow, ms_dedup, ms_stability, ms_total; /* device time per stage    */
+    /* the first 8 growth launches: node slots per unit, shared memory (1) or
+     * global arena (0), units, ms */
+    int32_t launch_cap[8], launch_smem[8];
+    int64_t launch_units[8];
+    double launch_ms[8];
 } mscd_run_stats;
 
 /* Text of a status code (static storage). */
@@ -102,6 +111,10 @@ const char *mscd_strerror(int status);
 
 /* Library version, major*10000 + minor*100 + patch. */
 int mscd_version(void);
+
+/* Number of kernels this library has launched in the calling process so far
+ * (all contexts); the difference around a call counts its launches. */
+int64_t mscd_launch_count(void);
 
 /* Create a context on CUDA device `device`.  params may be NULL.  Errors:
  * EINVAL (bad device or params), EDEVICE, ENOMEM. */

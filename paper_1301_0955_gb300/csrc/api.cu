@@ -7,6 +7,7 @@
 // node), deduplicates each scale and measures the stability between
 // successive scales.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -24,7 +25,7 @@ struct GraphRec {
     i32 *col = nullptr;
     float *w = nullptr;
     i64 *wfx = nullptr, *k = nullptr;
-    double *logk = nullptr;
+    float *logk = nullptr;
     DevGraph g;
 };
 
@@ -80,7 +81,11 @@ __global__ void widen_len(const i32 *ulen, i64 N, i64 *out) {
     for (i64 u = (i64)blockIdx.x * blockDim.x + threadIdx.x; u < N; u += (i64)gridDim.x * blockDim.x) out[u] = ulen[u];
 }
 
+std::atomic<long long> g_launches{0};
+
 }  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 struct mscd_ctx {
     int device = 0;
@@ -121,7 +126,6 @@ void free_run(mscd_ctx *c) {
     cudaFree(c->uf);
     cudaFree(c->ustat);
     cudaFree(c->ustatus);
-    cudaFree(c->out_nodes);
     c->alphas = nullptr;
     c->seeds = nullptr;
     c->uoff = nullptr;
@@ -130,8 +134,6 @@ void free_run(mscd_ctx *c) {
     c->uf = nullptr;
     c->ustat = nullptr;
     c->ustatus = nullptr;
-    c->out_nodes = nullptr;
-    c->out_cap = 0;
     for (auto &s : c->scales) scale_result_free(&s);
     c->scales.clear();
     c->nmi_succ.clear();
@@ -165,14 +167,15 @@ int ensure_arena(mscd_ctx *c, size_t bytes) {
     return MSCD_OK;
 }
 
-// Enlarge the unit output buffer, keeping what was written.
-int grow_output(mscd_ctx *c, i64 need, cudaStream_t st) {
+// Enlarge the unit output buffer (kept across runs), preserving its first
+// `keep` entries.
+int grow_output(mscd_ctx *c, i64 need, i64 keep, cudaStream_t st) {
     if (need <= c->out_cap) return MSCD_OK;
-    i64 cap = std::max<i64>(need + need / 4, 2 * c->out_cap);
+    i64 cap = std::max<i64>(need + need / 8, c->out_cap + c->out_cap / 2);
     i32 *nb = nullptr;
     MSCD_CUDA(cudaMalloc((void **)&nb, (size_t)cap * sizeof(i32)));
-    if (c->out_nodes && c->out_cap > 0)
-        MSCD_CUDA(cudaMemcpyAsync(nb, c->out_nodes, (size_t)c->out_cap * sizeof(i32), cudaMemcpyDeviceToDevice, st));
+    if (c->out_nodes && keep > 0)
+        MSCD_CUDA(cudaMemcpyAsync(nb, c->out_nodes, (size_t)keep * sizeof(i32), cudaMemcpyDeviceToDevice, st));
     MSCD_CUDA(cudaStreamSynchronize(st));
     cudaFree(c->out_nodes);
     c->out_nodes = nb;
@@ -197,8 +200,8 @@ void window_means(const std::vector<double> &nmi, int32_t S, int p, std::vector<
 }
 
 struct Task {
-    int cap;
-    std::vector<i64> units;  // empty + all = every unit
+    int cls;                 // index in the node-slot class ladder
+    std::vector<i64> units;  // the listed units, unless `all`
     bool all;
 };
 
@@ -228,6 +231,8 @@ const char *mscd_strerror(int s) {
 
 int mscd_version(void) { return 100; }
 
+int64_t mscd_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
 int mscd_create(mscd_ctx **out, int device, const mscd_params *params) {
     if (!out) return MSCD_EINVAL;
     *out = nullptr;
@@ -241,10 +246,13 @@ int mscd_create(mscd_ctx **out, int device, const mscd_params *params) {
     c->device = device;
     if (params) c->p = *params;
     if (c->p.warps_per_block <= 0) c->p.warps_per_block = 8;
-    if (c->p.smem_slots <= 0) c->p.smem_slots = 512;
     if (c->p.max_rounds <= 0) c->p.max_rounds = 1000000;
+    if (c->p.smem_slots < 0) c->p.smem_slots = 0;
+    if (c->p.mid_slots < 0) c->p.mid_slots = 0;
+    if (c->p.global_warps_per_sm <= 0) c->p.global_warps_per_sm = 16;
     if (c->p.warps_per_block > GROW_MAX_THREADS / 32 || (c->p.smem_slots & (c->p.smem_slots - 1)) ||
-        c->p.smem_slots < 32) {
+        (c->p.smem_slots > 0 && c->p.smem_slots < 32) || (c->p.mid_slots & (c->p.mid_slots - 1)) ||
+        (c->p.mid_slots > 0 && c->p.mid_slots < 32)) {
         delete c;
         return MSCD_EINVAL;
     }
@@ -264,6 +272,7 @@ int mscd_destroy(mscd_ctx *c) {
     free_run(c);
     for (auto &g : c->graphs) free_graph(g);
     cudaFree(c->arena);
+    cudaFree(c->out_nodes);
     cudaStreamDestroy(c->own);
     delete c;
     return MSCD_OK;
@@ -404,10 +413,9 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
         if ((rc = cuda_status(cudaMalloc((void **)&ctr, sizeof(Counters))))) break;
         if ((rc = cuda_status(cudaMalloc((void **)&retry_a, U1 * sizeof(i64))))) break;
         if ((rc = cuda_status(cudaMalloc((void **)&retry_b, U1 * sizeof(i64))))) break;
-        if ((rc = grow_output(c, std::max<i64>(U * 64, 1 << 20), st))) break;
         if (c->seeds) {
             if ((rc = cuda_status(cudaMemsetAsync(ctr, 0, sizeof(Counters), st)))) break;
-            check_seeds<<<152 * 8, 256, 0, st>>>(c->seeds, N, G.n, &ctr->error_flags);
+            check_seeds<<<152 * 8, 256, 0, st>>>(c->seeds, N, G.n, &ctr->error_flags); note_launch();
             u32 bad = 0;
             if ((rc = cuda_status(cudaMemcpyAsync(&bad, &ctr->error_flags, sizeof(u32), cudaMemcpyDeviceToHost, st))))
                 break;
@@ -415,14 +423,48 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
             if (bad) { rc = MSCD_EINVAL; break; }
         }
         // ---- growth: a task list of (slot class, units) ----
+        // Node-slot classes, one unit per warp: a shared-memory class of
+        // smem_slots (1024) and optionally one of mid_slots; then global-memory
+        // arenas of 8x the capacity per class, up to the first power of two
+        // above the node count (never overflows), run at global_warps_per_sm.
+        std::vector<int> ladder;
+        std::vector<bool> in_smem;
+        {
+            const size_t smem_budget = 220 * 1024;
+            int c0 = c->p.smem_slots;
+            if (c0 == 0) c0 = grow_state_bytes(G, 1024) * 4 <= smem_budget ? 1024 : 512;
+            ladder.push_back(c0);
+            if (c->p.mid_slots > ladder.back() && grow_state_bytes(G, c->p.mid_slots) <= smem_budget)
+                ladder.push_back(c->p.mid_slots);
+            in_smem.assign(ladder.size(), true);
+            i64 full = 32;
+            while (full < G.n + 1) full <<= 1;
+            i64 cg = ladder.back();
+            while (cg < full) {
+                cg = std::min<i64>(cg * 8, full);
+                ladder.push_back((int)cg);
+                in_smem.push_back(false);
+            }
+        }
         std::vector<Task> tasks;
-        if (U > 0) tasks.push_back(Task{c->p.smem_slots, {}, true});
-        const int wpb = c->p.warps_per_block;
+        if (U > 0) tasks.push_back(Task{0, {}, true});
         unsigned long long cursor = 0;
+        size_t free_mem = 0, total_mem = 0;
+        cudaMemGetInfo(&free_mem, &total_mem);
+        const i64 out_budget = (i64)(free_mem / 4 / sizeof(i32));  // output may take a quarter of free memory
         while (!tasks.empty() && rc == MSCD_OK) {
             Task t = std::move(tasks.front());
             tasks.erase(tasks.begin());
+            const int cap = ladder[t.cls];
+            const bool sm = in_smem[t.cls];
             const i64 n_work = t.all ? U : (i64)t.units.size();
+            // room for every list this launch can write (<= min(cap, n) each) when
+            // that fits the budget; otherwise units that find it full are retried
+            {
+                const i64 bound = (i64)cursor + n_work * std::min<i64>(cap, std::max<i64>(G.n, 1));
+                const i64 want = std::min<i64>(bound, std::max<i64>(out_budget, (i64)cursor + n_work * 64));
+                if ((rc = grow_output(c, want, (i64)cursor, st))) break;
+            }
             if ((rc = cuda_status(cudaMemsetAsync(ctr, 0, sizeof(Counters), st)))) break;
             GrowArgs a{};
             a.G = G;
@@ -431,7 +473,7 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
             a.n_seeds = N;
             a.n_work = n_work;
             a.work_counter = &ctr->work;
-            a.cap = t.cap;
+            a.cap = cap;
             a.max_rounds = c->p.max_rounds;
             a.out_nodes = c->out_nodes;
             a.out_cursor = &ctr->out_cursor;
@@ -448,7 +490,8 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
             a.retry_out = retry_b;
             a.n_retry_out = &ctr->n_retry_out;
             a.error_flags = &ctr->error_flags;
-            a.state_bytes = grow_state_bytes(t.cap);
+            a.state_bytes = grow_state_bytes(G, cap);
+            a.log_kmax = G.kmax > 1 ? (float)std::log((double)G.kmax) : 0.0f;
             i64 *list_dev = nullptr;
             if (!t.all) {
                 if ((rc = cuda_status(cudaMallocAsync((void **)&list_dev, n_work * sizeof(i64), st)))) break;
@@ -461,33 +504,53 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
             if ((rc = cuda_status(cudaMemcpyAsync(&ctr->out_cursor, &cursor, sizeof(cursor), cudaMemcpyHostToDevice,
                                                   st))))
                 break;
-            const bool smem_class = t.cap == c->p.smem_slots;
-            int blocks = 0, threads = wpb * 32;
+            int blocks = 0, threads = 32;
             size_t smem = 0;
-            if (smem_class) {
+            if (sm) {
+                // as many one-warp units per CTA as fit 220 KiB (<= 16), one CTA per SM
                 a.use_smem = 1;
-                smem = (size_t)wpb * a.state_bytes;
+                const int wpc = (int)std::max<size_t>(1, std::min<size_t>(16, (220 * 1024) / a.state_bytes));
+                threads = 32 * wpc;
+                smem = (size_t)wpc * a.state_bytes;
                 int per_sm = 0;
-                if ((rc = grow_occupancy(threads, smem, &per_sm))) break;
-                if (c->p.blocks_per_sm > 0) per_sm = std::min(per_sm, c->p.blocks_per_sm);
+                if ((rc = grow_occupancy(a, threads, smem, &per_sm))) break;
+                if (t.cls == 0 && c->p.blocks_per_sm > 0) per_sm = std::min(per_sm, c->p.blocks_per_sm);
                 if (per_sm < 1) { rc = MSCD_EINVAL; break; }
                 blocks = per_sm * c->sm_count;
             } else {
                 a.use_smem = 0;
+                const int wpc = c->p.warps_per_block;
                 const size_t budget = (size_t)4 << 30;
-                i64 warps = std::max<i64>(1, std::min<i64>((i64)(budget / a.state_bytes), (i64)c->sm_count * 16));
+                i64 warps = std::max<i64>(
+                    1, std::min<i64>((i64)(budget / a.state_bytes), (i64)c->sm_count * c->p.global_warps_per_sm));
                 warps = std::min<i64>(warps, std::max<i64>(n_work, 1));
-                threads = (int)std::min<i64>(warps, wpb) * 32;
+                threads = (int)std::min<i64>(warps, wpc) * 32;
                 blocks = (int)((warps + threads / 32 - 1) / (threads / 32));
                 if ((rc = ensure_arena(c, (size_t)blocks * (threads / 32) * a.state_bytes))) break;
                 a.gstate = c->arena;
             }
             blocks = (int)std::max<i64>(1, std::min<i64>(blocks, (n_work + threads / 32 - 1) / (threads / 32)));
+            cudaEvent_t l0, l1;
+            cudaEventCreate(&l0);
+            cudaEventCreate(&l1);
+            cudaEventRecord(l0, st);
             if ((rc = grow_launch(a, blocks, threads, smem, st))) break;
-            c->stats.grow_launches++;
+            cudaEventRecord(l1, st);
             Counters h{};
             if ((rc = cuda_status(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st)))) break;
             if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+            if (c->stats.grow_launches < 8) {
+                const int r = (int)c->stats.grow_launches;
+                float lms = 0.0f;
+                cudaEventElapsedTime(&lms, l0, l1);
+                c->stats.launch_cap[r] = cap;
+                c->stats.launch_smem[r] = sm ? 1 : 0;
+                c->stats.launch_units[r] = n_work;
+                c->stats.launch_ms[r] = lms;
+            }
+            cudaEventDestroy(l0);
+            cudaEventDestroy(l1);
+            c->stats.grow_launches++;
             if (list_dev) cudaFree(list_dev);
             if (h.error_flags) { rc = MSCD_EDEVICE; break; }
             if (!h.n_retry_out) {
@@ -501,8 +564,8 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
                                                  cudaMemcpyDeviceToHost))))
                     break;
                 cursor = (unsigned long long)c->out_cap;
-                if ((rc = grow_output(c, c->out_cap + (i64)h.out_needed + (1 << 20), st))) break;
-                tasks.insert(tasks.begin(), Task{t.cap, std::move(lst), false});
+                if ((rc = grow_output(c, c->out_cap + (i64)h.out_needed + (1 << 20), (i64)cursor, st))) break;
+                tasks.insert(tasks.begin(), Task{t.cls, std::move(lst), false});
             }
             if (h.n_retry_state) {
                 std::vector<i64> lst(h.n_retry_state);
@@ -510,12 +573,8 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
                                                  cudaMemcpyDeviceToHost))))
                     break;
                 c->stats.overflow_units += (i64)lst.size();
-                i64 next = (i64)t.cap * 8;
-                i64 full = 32;
-                while (full < G.n + 1) full <<= 1;
-                next = std::min(next, full);
-                if (next <= t.cap) { rc = MSCD_EDEVICE; break; }
-                tasks.push_back(Task{(int)next, std::move(lst), false});
+                if (t.cls + 1 >= (int)ladder.size()) { rc = MSCD_EDEVICE; break; }
+                tasks.push_back(Task{t.cls + 1, std::move(lst), false});
             }
         }
         if (rc) break;
@@ -524,7 +583,7 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
         unsigned long long *tot = nullptr;
         if ((rc = cuda_status(cudaMallocAsync((void **)&tot, 8 * sizeof(unsigned long long), st)))) break;
         cudaMemsetAsync(tot, 0, 8 * sizeof(unsigned long long), st);
-        if (U > 0) sum_unit_stats<<<152 * 4, 256, 0, st>>>(c->ustat, c->ulen, c->ustatus, U, tot);
+        if (U > 0) { sum_unit_stats<<<152 * 4, 256, 0, st>>>(c->ustat, c->ulen, c->ustatus, U, tot); note_launch(); }
         unsigned long long ht[8];
         cudaMemcpyAsync(ht, tot, sizeof(ht), cudaMemcpyDeviceToHost, st);
         cudaFreeAsync(tot, st);
@@ -606,7 +665,7 @@ int mscd_get_memberships(mscd_ctx *c, int32_t scale_idx, int64_t *ptr, int32_t *
     int rc = MSCD_OK;
     do {
         if ((rc = cuda_status(cudaMallocAsync((void **)&dptr, (N + 1) * sizeof(i64), st)))) break;
-        if (N > 0) widen_len<<<152 * 4, 256, 0, st>>>(c->ulen + base, N, dptr);
+        if (N > 0) { widen_len<<<152 * 4, 256, 0, st>>>(c->ulen + base, N, dptr); note_launch(); }
         if ((rc = scan_exclusive_i64(dptr, dptr, N, dptr + N, st))) break;
         i64 total = 0;
         if ((rc = cuda_status(cudaMemcpyAsync(&total, dptr + N, sizeof(i64), cudaMemcpyDeviceToHost, st)))) break;
@@ -623,7 +682,7 @@ int mscd_get_memberships(mscd_ctx *c, int32_t scale_idx, int64_t *ptr, int32_t *
         if (nodes_cap < total || (total > 0 && !nodes)) { rc = MSCD_ESMALL; break; }
         if (total > 0) {
             if ((rc = cuda_status(cudaMallocAsync((void **)&dnodes, total * sizeof(i32), st)))) break;
-            gather_lists<<<152 * 8, 256, 0, st>>>(c->uoff + base, c->ulen + base, dptr, c->out_nodes, N, dnodes);
+            gather_lists<<<152 * 8, 256, 0, st>>>(c->uoff + base, c->ulen + base, dptr, c->out_nodes, N, dnodes); note_launch();
             if ((rc = cuda_status(cudaMemcpyAsync(nodes, dnodes, total * sizeof(i32), cudaMemcpyDeviceToHost, st))))
                 break;
         }

@@ -20,7 +20,8 @@ struct DevGraph {
     const i32 *col = nullptr;    // int32[nnz]
     const i64 *wfx = nullptr;    // int64[nnz] exact fixed-point weights, null = unweighted
     const i64 *k = nullptr;      // int64[n] weighted degree (weight units)
-    const double *logk = nullptr;  // double[n] log(k) (0 where k = 0)
+    const float *logk = nullptr;   // float[n] logf(k) (0 where k = 0), for the binary32 priority keys
+    i64 kmax = 0;                  // largest k_u
     int unit_exp = 0;            // weight unit 2^unit_exp
     i64 volume = 0;              // sum of k
 };
@@ -37,10 +38,13 @@ static inline int cuda_status(cudaError_t e) {
         if (_e != cudaSuccess) return cuda_status(_e); \
     } while (0)
 
+// Count one kernel launch of this library (process-wide, see mscd_launch_count).
+void note_launch();
+
 // Device-side exclusive scan of int64 (in place allowed); returns the total
 // through *total_dev (device pointer, may be null).  Work buffer handled inside.
 int scan_exclusive_i64(const i64 *in, i64 *out, i64 n, i64 *total_dev, cudaStream_t st);
 
 // Graph preparation (checks, exact weights, degrees, log degrees).
 int graph_prepare(i64 n, const i64 *rp_dev, const i32 *col_dev, const float *w_dev, DevGraph *g, i64 **wfx_out,
-                  i64 **k_out, double **logk_out, cudaStream_t st);
+                  i64 **k_out, float **logk_out, cudaStream_t st);

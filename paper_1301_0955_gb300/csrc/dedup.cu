@@ -86,8 +86,8 @@ __global__ void mark_reps(const i64 *urep, i64 N, i64 *flag) {
         flag[u] = urep[u] == u ? 1 : 0;
 }
 
-__global__ void fill_comms(const i64 *urep, const i64 *cid, const i32 *ulen, const double *uf, i64 N, i64 *clen,
-                           double *cf, i64 *crep, i32 *seed2comm) {
+__global__ void fill_comms(const i64 *urep, const i64 *cid, const i32 *ulen, const double *uf, const u64 *uhash,
+                           i64 N, i64 *clen, double *cf, u64 *chash, i64 *crep, i32 *seed2comm) {
     for (i64 u = (i64)blockIdx.x * blockDim.x + threadIdx.x; u < N; u += (i64)gridDim.x * blockDim.x) {
         const i64 r = urep[u];
         seed2comm[u] = (i32)cid[r];
@@ -95,6 +95,7 @@ __global__ void fill_comms(const i64 *urep, const i64 *cid, const i32 *ulen, con
             const i64 c = cid[u];
             clen[c] = ulen[u];
             cf[c] = uf[u];
+            chash[c] = uhash[u];
             crep[c] = u;
         }
     }
@@ -118,6 +119,7 @@ void scale_result_free(ScaleResult *r) {
     cudaFree(r->comm_nodes);
     cudaFree(r->comm_f);
     cudaFree(r->seed2comm);
+    cudaFree(r->comm_hash);
     *r = ScaleResult{};
 }
 
@@ -153,16 +155,16 @@ int dedup_scale(const i64 *uoff, const i32 *ulen, const u64 *uhash, const double
         if ((rc = cuda_status(cudaMemsetAsync(tkey, 0, T * sizeof(u64), st)))) break;
         if ((rc = cuda_status(cudaMemsetAsync(trep, 0x7f, T * sizeof(i64), st)))) break;
         if ((rc = cuda_status(cudaMemsetAsync(tot, 0, 2 * sizeof(i64) + 2 * sizeof(unsigned long long), st)))) break;
-        table_insert<<<blocks, 256, 0, st>>>(uhash, N, tkey, trep, T - 1, uent, err);
-        verify<<<wblocks, 256, 0, st>>>(uoff, ulen, nodes, uent, trep, N, urep, ncoll);
+        table_insert<<<blocks, 256, 0, st>>>(uhash, N, tkey, trep, T - 1, uent, err); note_launch();
+        verify<<<wblocks, 256, 0, st>>>(uoff, ulen, nodes, uent, trep, N, urep, ncoll); note_launch();
         unsigned long long h_coll = 0;
         u32 h_err = 0;
         if ((rc = cuda_status(cudaMemcpyAsync(&h_coll, ncoll, sizeof(h_coll), cudaMemcpyDeviceToHost, st)))) break;
         if ((rc = cuda_status(cudaMemcpyAsync(&h_err, err, sizeof(h_err), cudaMemcpyDeviceToHost, st)))) break;
         if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
         if (h_err) { rc = MSCD_EDEVICE; break; }
-        if (h_coll) regroup_collisions<<<1, 32, 0, st>>>(uoff, ulen, nodes, N, urep);
-        mark_reps<<<blocks, 256, 0, st>>>(urep, N, flag);
+        if (h_coll) { regroup_collisions<<<1, 32, 0, st>>>(uoff, ulen, nodes, N, urep); note_launch(); }
+        mark_reps<<<blocks, 256, 0, st>>>(urep, N, flag); note_launch();
         if ((rc = scan_exclusive_i64(flag, cid, N, tot, st))) break;
         i64 C = 0;
         if ((rc = cuda_status(cudaMemcpyAsync(&C, tot, sizeof(i64), cudaMemcpyDeviceToHost, st)))) break;
@@ -173,7 +175,9 @@ int dedup_scale(const i64 *uoff, const i32 *ulen, const u64 *uhash, const double
         if ((rc = cuda_status(cudaMalloc((void **)&out->comm_ptr, (C + 1) * sizeof(i64))))) break;
         if ((rc = cuda_status(cudaMalloc((void **)&out->comm_f, std::max<i64>(C, 1) * sizeof(double))))) break;
         if ((rc = cuda_status(cudaMalloc((void **)&out->seed2comm, N * sizeof(i32))))) break;
-        fill_comms<<<blocks, 256, 0, st>>>(urep, cid, ulen, uf, N, clen, out->comm_f, crep, out->seed2comm);
+        if ((rc = cuda_status(cudaMalloc((void **)&out->comm_hash, std::max<i64>(C, 1) * sizeof(u64))))) break;
+        fill_comms<<<blocks, 256, 0, st>>>(urep, cid, ulen, uf, uhash, N, clen, out->comm_f, out->comm_hash, crep,
+                                           out->seed2comm); note_launch();
         if ((rc = scan_exclusive_i64(clen, out->comm_ptr, C, out->comm_ptr + C, st))) break;
         i64 total = 0;
         if ((rc = cuda_status(cudaMemcpyAsync(&total, out->comm_ptr + C, sizeof(i64), cudaMemcpyDeviceToHost, st))))
@@ -182,7 +186,7 @@ int dedup_scale(const i64 *uoff, const i32 *ulen, const u64 *uhash, const double
         out->n_nodes = total;
         if ((rc = cuda_status(cudaMalloc((void **)&out->comm_nodes, std::max<i64>(total, 1) * sizeof(i32))))) break;
         const unsigned cblocks = (unsigned)std::max<i64>(1, std::min<i64>((C + 7) / 8, 152 * 16));
-        if (C > 0) copy_lists<<<cblocks, 256, 0, st>>>(crep, out->comm_ptr, uoff, nodes, C, out->comm_nodes);
+        if (C > 0) { copy_lists<<<cblocks, 256, 0, st>>>(crep, out->comm_ptr, uoff, nodes, C, out->comm_nodes); note_launch(); }
         rc = cuda_status(cudaGetLastError());
     } while (0);
     cudaFreeAsync(tkey, st);

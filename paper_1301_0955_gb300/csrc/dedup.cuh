@@ -9,6 +9,7 @@ struct ScaleResult {
     i32 *comm_nodes = nullptr; // [n_nodes]
     double *comm_f = nullptr;  // [n_comms]
     i32 *seed2comm = nullptr;  // [n_seeds]
+    u64 *comm_hash = nullptr;  // [n_comms] hash of the member list
 };
 
 void scale_result_free(ScaleResult *r);

@@ -9,6 +9,7 @@
 //                                     a = d1/d2,   b = k1/k2
 // The sign is the true mathematical sign, decided in stages:
 //   1. integer shortcuts (b1 == b2 or a1 == a2);
+//   1b. (add / remove tests) binary32 with a derived bound, see sign_delta32;
 //   2. binary64 with a derived bound: each log-ratio term has absolute error
 //      <= 13u|L| (u = 2^-53: 3u from the quotient, <= 1 ulp from log1p/log,
 //      derivative bound 2 on the log1p branch, |L| > log 1.5 on the log
@@ -196,6 +197,7 @@ __device__ __noinline__ int sign_slow(i64 a1, i64 a2, i64 b1, i64 b2, double alp
     return 0;
 }
 
+// Binary64 stage and beyond (integer shortcuts first).
 __device__ __forceinline__ int sign_delta(i64 a1, i64 a2, i64 b1, i64 b2, double alpha, u32 *flags) {
     if (b1 == b2) return (a1 > a2) - (a1 < a2);
     if (a1 == a2) return (b2 > b1) - (b2 < b1);
@@ -207,31 +209,58 @@ __device__ __forceinline__ int sign_delta(i64 a1, i64 a2, i64 b1, i64 b2, double
     return sign_slow(a1, a2, b1, b2, alpha, flags);
 }
 
+// Binary32 stage in front of sign_delta (GB300 issues binary32 at many times
+// the binary64 rate).  The same analysis as the binary64 stage with
+// u32 = 2^-24: each log-ratio term is within 13 u32 |L| (quotient rounded
+// three times, <= 1 ulp from log1pf / logf), alpha32 = fl(alpha) adds
+// u32 alpha |L2|, the fused multiply-add one more rounding; the sign is taken
+// when |Delta| > 2^-18 (|L1| + alpha |L2|) = 64 u32 (...).
+__device__ __forceinline__ float log_ratio32(i64 a1, i64 a2) {
+    i64 diff = a1 - a2;
+    u64 ad = diff < 0 ? (u64)(-diff) : (u64)diff;
+    if (ad <= (u64)a2 / 2) return log1pf((float)diff / (float)a2);
+    return logf((float)a1 / (float)a2);
+}
+
+__device__ __forceinline__ int sign_delta32(i64 a1, i64 a2, i64 b1, i64 b2, double alpha, float alpha32,
+                                            u32 *flags) {
+    if (b1 == b2) return (a1 > a2) - (a1 < a2);
+    if (a1 == a2) return (b2 > b1) - (b2 < b1);
+    float L1 = log_ratio32(a1, a2), L2 = log_ratio32(b1, b2);
+    float D = fmaf(-alpha32, L2, L1);
+    float E = 0x1p-18f * (fabsf(L1) + alpha32 * fabsf(L2));
+    if (D > E) return 1;
+    if (D < -E) return -1;
+    return sign_delta(a1, a2, b1, b2, alpha, flags);
+}
+
 // Add test for a node outside c: (K+2d)/(V+k)^alpha > K/V^alpha.
-__device__ __forceinline__ bool add_test(i64 K, i64 V, i64 d, i64 k, double alpha, u32 *flags) {
+__device__ __forceinline__ bool add_test(i64 K, i64 V, i64 d, i64 k, double alpha, float alpha32, u32 *flags) {
     if (K == 0) return true;  // f_c = 0 < f_{c+n} because d > 0
-    return sign_delta(K + 2 * d, K, V + k, V, alpha, flags) > 0;
+    return sign_delta32(K + 2 * d, K, V + k, V, alpha, alpha32, flags) > 0;
 }
 
 // Remove test for a member: (K-2d)/(V-k)^alpha > K/V^alpha.
-__device__ __forceinline__ bool remove_test(i64 K, i64 V, i64 d, i64 k, double alpha, u32 *flags) {
+__device__ __forceinline__ bool remove_test(i64 K, i64 V, i64 d, i64 k, double alpha, float alpha32, u32 *flags) {
     if (K == 0 || K - 2 * d == 0) return false;  // f_{c\n} = 0 <= f_c
-    return sign_delta(K - 2 * d, K, V - k, V, alpha, flags) > 0;
+    return sign_delta32(K - 2 * d, K, V - k, V, alpha, alpha32, flags) > 0;
 }
 
 // Necessary conditions (cheap filters, no transcendental): log1p(x) <= x and
 // log1p(y) >= y/(1+y) give   add  => 2d(V+k) > alpha K k,
 //                            remove => 2d(V-k) < alpha K k.
-// The 2^-40 margin covers the binary64 rounding of both products.
-__device__ __forceinline__ bool add_possible(i64 K, i64 V, i64 d, i64 k, double alpha) {
-    double lhs = 2.0 * (double)d * ((double)V + (double)k);
-    double rhs = alpha * (double)K * (double)k;
-    return lhs > rhs * (1.0 - 0x1p-40);
+// Evaluated in binary32 (products stay below 2^125 < FLT_MAX); each side
+// carries at most ~6 roundings of 2^-24 (alpha32 included), so a 2^-19
+// margin keeps the filters one-sided.
+__device__ __forceinline__ bool add_possible(i64 K, i64 V, i64 d, i64 k, float alpha32) {
+    float lhs = 2.0f * (float)d * (float)(V + k);  // V + k formed exactly in int64
+    float rhs = alpha32 * (float)K * (float)k;
+    return lhs > rhs * (1.0f - 0x1p-19f);
 }
-__device__ __forceinline__ bool remove_possible(i64 K, i64 V, i64 d, i64 k, double alpha) {
-    double lhs = 2.0 * (double)d * ((double)V - (double)k);
-    double rhs = alpha * (double)K * (double)k;
-    return lhs < rhs * (1.0 + 0x1p-40);
+__device__ __forceinline__ bool remove_possible(i64 K, i64 V, i64 d, i64 k, float alpha32) {
+    float lhs = 2.0f * (float)d * (float)(V - k);  // no cancellation: V - k exact in int64
+    float rhs = alpha32 * (float)K * (float)k;
+    return lhs < rhs * (1.0f + 0x1p-19f);
 }
 
 }  // namespace exact

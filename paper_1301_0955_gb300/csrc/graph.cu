@@ -29,6 +29,7 @@ struct PrepState {
     int min_lowbit;
     unsigned long long total;  // exact volume (valid while total_d < 2^63)
     double total_d;            // coarse volume, guards against wrap-around
+    unsigned long long kmax;   // largest degree
 };
 
 __global__ void check_row_ptr(const i64 *rp, i64 n, PrepState *ps) {
@@ -114,10 +115,10 @@ __global__ void fixed_weights(const float *w, i64 nnz, int ue, i64 *wfx, PrepSta
 }
 
 // Warp per row: k_u = sum of weights (exact), log k_u, and the volume.
-__global__ void degrees(const i64 *rp, const i64 *wfx, i64 n, i64 *k, double *logk, PrepState *ps) {
+__global__ void degrees(const i64 *rp, const i64 *wfx, i64 n, i64 *k, float *logk, PrepState *ps) {
     const int lane = threadIdx.x & 31;
     const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
-    unsigned long long tot = 0;
+    unsigned long long tot = 0, kmax = 0;
     double tot_d = 0.0;
     for (i64 u = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
         const i64 rs = rp[u], re = rp[u + 1];
@@ -138,14 +139,16 @@ __global__ void degrees(const i64 *rp, const i64 *wfx, i64 n, i64 *k, double *lo
         }
         if (lane == 0) {
             k[u] = (i64)s;
-            logk[u] = s ? log((double)(i64)s) : 0.0;
+            logk[u] = s ? logf((float)(i64)s) : 0.0f;
             tot += s;
+            kmax = s > kmax ? s : kmax;
             tot_d += sd;
         }
     }
     if (lane == 0) {
         atomicAdd(&ps->total, tot);
         atomicAdd(&ps->total_d, tot_d);
+        atomicMax(&ps->kmax, kmax);
     }
 }
 
@@ -163,26 +166,26 @@ int first_category(u32 mask) {
 }  // namespace
 
 int graph_prepare(i64 n, const i64 *rp, const i32 *col, const float *w, DevGraph *g, i64 **wfx_out, i64 **k_out,
-                  double **logk_out, cudaStream_t st) {
+                  float **logk_out, cudaStream_t st) {
     *wfx_out = nullptr;
     *k_out = nullptr;
     *logk_out = nullptr;
     PrepState *ps = nullptr;
-    PrepState init{0u, INT32_MAX, 0ull, 0.0};
+    PrepState init{0u, INT32_MAX, 0ull, 0.0, 0ull};
     MSCD_CUDA(cudaMallocAsync((void **)&ps, sizeof(PrepState), st));
     int rc = MSCD_OK;
     PrepState h{};
     i64 nnz = 0;
     do {
         if ((rc = cuda_status(cudaMemcpyAsync(ps, &init, sizeof(init), cudaMemcpyHostToDevice, st)))) break;
-        check_row_ptr<<<(unsigned)((n + 1 + 255) / 256), 256, 0, st>>>(rp, n, ps);
+        check_row_ptr<<<(unsigned)((n + 1 + 255) / 256), 256, 0, st>>>(rp, n, ps); note_launch();
         if ((rc = cuda_status(cudaMemcpyAsync(&h, ps, sizeof(h), cudaMemcpyDeviceToHost, st)))) break;
         if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
         if (h.mask) { rc = MSCD_EINVAL; break; }
         if ((rc = cuda_status(cudaMemcpyAsync(&nnz, rp + n, sizeof(i64), cudaMemcpyDeviceToHost, st)))) break;
         if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
         const unsigned row_blocks = (unsigned)std::max<i64>(1, std::min<i64>((n + 7) / 8, 152 * 64));
-        if (n > 0) check_entries<<<row_blocks, 256, 0, st>>>(rp, col, w, n, ps);
+        if (n > 0) { check_entries<<<row_blocks, 256, 0, st>>>(rp, col, w, n, ps); note_launch(); }
         if ((rc = cuda_status(cudaMemcpyAsync(&h, ps, sizeof(h), cudaMemcpyDeviceToHost, st)))) break;
         if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
         if ((rc = first_category(h.mask))) break;
@@ -191,11 +194,11 @@ int graph_prepare(i64 n, const i64 *rp, const i32 *col, const float *w, DevGraph
             ue = h.min_lowbit;
             if ((rc = cuda_status(cudaMalloc((void **)wfx_out, (size_t)nnz * sizeof(i64))))) break;
             fixed_weights<<<(unsigned)std::min<i64>((nnz + 255) / 256, 152 * 32), 256, 0, st>>>(w, nnz, ue,
-                                                                                             *wfx_out, ps);
+                                                                                             *wfx_out, ps); note_launch();
         }
         if ((rc = cuda_status(cudaMalloc((void **)k_out, (size_t)std::max<i64>(n, 1) * sizeof(i64))))) break;
-        if ((rc = cuda_status(cudaMalloc((void **)logk_out, (size_t)std::max<i64>(n, 1) * sizeof(double))))) break;
-        if (n > 0) degrees<<<row_blocks, 256, 0, st>>>(rp, *wfx_out, n, *k_out, *logk_out, ps);
+        if ((rc = cuda_status(cudaMalloc((void **)logk_out, (size_t)std::max<i64>(n, 1) * sizeof(float))))) break;
+        if (n > 0) { degrees<<<row_blocks, 256, 0, st>>>(rp, *wfx_out, n, *k_out, *logk_out, ps); note_launch(); }
         if ((rc = cuda_status(cudaMemcpyAsync(&h, ps, sizeof(h), cudaMemcpyDeviceToHost, st)))) break;
         if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
         if ((rc = first_category(h.mask))) break;
@@ -209,6 +212,7 @@ int graph_prepare(i64 n, const i64 *rp, const i32 *col, const float *w, DevGraph
         g->logk = *logk_out;
         g->unit_exp = ue;
         g->volume = (i64)h.total;
+        g->kmax = (i64)h.kmax;
     } while (0);
     cudaFreeAsync(ps, st);
     if (rc != MSCD_OK) {

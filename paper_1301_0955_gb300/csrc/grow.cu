@@ -16,48 +16,92 @@
 // node added next is the highest-ranked queued node that passes the test,
 // and every queued node ranked before it is popped and rejected on the way.
 // The warp finds it with one pass over the node slots (filter by a necessary
-// condition, exact test on the survivors, exact argmax), so the cost of a
-// long run of rejections is one pass instead of one pop each.  The common
-// case (the top node passes) is a plain exact argmax.  Likewise a prune pass
+// condition, exact test on the survivors, exact argmax), so a long run of
+// rejections costs one pass instead of one pop each.  The common case (the
+// top node passes) is an exact argmax over the queue.  Likewise a prune pass
 // finds the smallest-id member that passes the remove test in one pass,
 // removes it and continues after it.
 //
-// State per warp: node slots (id, d_in, k, priority key, flags) and an
-// open-addressing hash node -> slot, either in shared memory (small class)
-// or in a global-memory arena (large classes).  A unit whose touched nodes
-// exceed the class capacity stops, is listed, and is grown again in a larger
-// class; the result does not depend on the class.
+// Ranking keys are binary32 log d - alpha log k, compared with a certified
+// bound; pairs closer than the bound are ordered by the exact comparator.
+// With u32 = 2^-24 and L = log of the largest degree, a key carries at most
+// u32 (1+alpha) + 3 u32 |log d| + 5 u32 alpha |log k| <= 5 u32 (1+alpha)(1+L)
+// of error (conversions, <= 1 ulp logf twice, fl(alpha), product,
+// difference); E = 2^-20 (1+alpha)(1+L) per key is above it.
+//
+// Queue argmax: the slots are split into groups of 32 and each group keeps an
+// upper bound of its largest key (raised by atomicMax when a key rises, left
+// stale when a key is removed).  A pop recomputes exactly every group whose
+// bound is within 2E of the largest bound, and repeats while the largest
+// bound drops; the best node is then in a recomputed group (a group left out
+// has a bound, hence a true maximum, below the true maximum minus 2E), so the
+// result is the exact argmax at the cost of a few groups.
+//
+// State per warp: node slots (d_in, k, key, id, flags), group bounds and an
+// open-addressing hash node -> slot, in shared memory (first class) or in a
+// global-memory arena (larger classes, run at high occupancy so that the
+// dependent steps of one unit overlap with those of many others).  A unit
+// whose touched nodes exceed the class capacity stops, is listed, and is
+// grown again in a larger class; the result does not depend on the class or
+// on slot order.
 #include "common.cuh"
 #include "exact.cuh"
 #include "grow.cuh"
 
 namespace {
 
-constexpr u32 F_MEMBER = 1u;
-constexpr double NEG_INF = -__builtin_huge_val();
+constexpr unsigned char F_MEMBER = 1u;
 
+// Order-preserving int image of a binary32 value (no NaNs occur).
+__device__ __forceinline__ int ord(float f) {
+    const int b = __float_as_int(f);
+    return b >= 0 ? b : b ^ 0x7fffffff;
+}
+__device__ __forceinline__ float unord(int o) { return __int_as_float(o >= 0 ? o : o ^ 0x7fffffff); }
+constexpr int ORD_NEG_INF = (int)(0xff800000u ^ 0x7fffffffu);
+constexpr float NEG_INF = -__builtin_huge_valf();
+
+// VT: type of d_in and k in the slots; HT: type of a hash bucket (slot + 1).
+template <class VT, class HT, bool WEIGHTED>
 struct State {
-    double *key;  // priority key (log d - alpha log k) while queued, else -inf
-    i64 *din;     // d_in(u, c)
-    i64 *kdeg;    // k_u
-    i32 *id;      // node id
-    i32 *hpos;    // hash bucket of the slot
-    u32 *hsh;     // bucket -> slot + 1 (0 = empty)
-    unsigned char *flag;
-    int C, H;     // slot capacity, hash buckets (2C)
+    VT *din;              // [C] d_in(u, c)
+    VT *kdeg;             // [C] k_u
+    float *key;           // [C] ranking key while queued, else -inf
+    i32 *id;              // [C] node id
+    int *gmax;            // [C/32] upper bound of the group's largest key (ord image)
+    HT *hsh;              // [2C] bucket -> slot + 1 (0 = empty)
+    unsigned char *flag;  // [C]
+    int C, H;
 };
 
-__device__ __forceinline__ State carve(unsigned char *base, int C) {
-    State s;
+// Rounded up to 128 bytes: per-warp states are laid end to end, and the
+// 8-byte slot arrays must stay aligned for every warp.
+template <class VT, class HT, bool WEIGHTED>
+__host__ __device__ __forceinline__ size_t state_bytes_t(int C) {
+    const size_t per = 2 * sizeof(VT) + 4 + 4 + 2 * sizeof(HT) + 1;
+    const size_t b = (size_t)C * per + 4 * (size_t)(C / 32);
+    return (b + 127) & ~(size_t)127;
+}
+
+template <class VT, class HT, bool WEIGHTED>
+__device__ __forceinline__ State<VT, HT, WEIGHTED> carve(unsigned char *base, int C) {
+    State<VT, HT, WEIGHTED> s;
     s.C = C;
     s.H = 2 * C;
-    s.key = (double *)base;
-    s.din = (i64 *)(base + 8ull * C);
-    s.kdeg = (i64 *)(base + 16ull * C);
-    s.id = (i32 *)(base + 24ull * C);
-    s.hpos = (i32 *)(base + 28ull * C);
-    s.hsh = (u32 *)(base + 32ull * C);
-    s.flag = base + 40ull * C;
+    size_t o = 0;
+    s.din = (VT *)(base + o);
+    o += sizeof(VT) * (size_t)C;
+    s.kdeg = (VT *)(base + o);
+    o += sizeof(VT) * (size_t)C;
+    s.key = (float *)(base + o);
+    o += 4 * (size_t)C;
+    s.id = (i32 *)(base + o);
+    o += 4 * (size_t)C;
+    s.gmax = (int *)(base + o);
+    o += 4 * (size_t)(C / 32);
+    s.hsh = (HT *)(base + o);
+    o += 2 * sizeof(HT) * (size_t)C;
+    s.flag = base + o;
     return s;
 }
 
@@ -82,15 +126,36 @@ struct Unit {
     i64 K, V;
     int ns;  // slots in use
     i32 seed;
-    double alpha, E2;
+    double alpha;
+    float alpha32, E2;
     i64 edges, adds, removes, rounds;
-    u32 xflags;  // EXACT_* of every decision
+    u32 xflags;  // EXACT_* of this lane's decisions
     bool ovf;    // slot capacity exceeded
-    bool err;    // internal probe bound hit (cannot happen at load <= 1/2)
+    bool err;    // probe bound hit (cannot happen at load <= 1/2)
 };
 
+// Claim an empty bucket h for slot s (false if it was taken meanwhile).
+template <class HT>
+__device__ __forceinline__ bool claim_bucket(HT *hsh, u32 h, int s) {
+    if (sizeof(HT) == 4) return atomicCAS((u32 *)&hsh[h], 0u, (u32)(s + 1)) == 0u;
+    // 16-bit buckets: compare-and-swap on the aligned word holding the bucket
+    // (the bucket array is 4-byte aligned with an even length).  Each failure
+    // means one of the word's two buckets was filled, so it fails at most twice.
+    u32 *word = (u32 *)((uintptr_t)&hsh[h] & ~(uintptr_t)3);
+    const int sh = ((uintptr_t)&hsh[h] & 2) ? 16 : 0;
+    u32 old = *word;
+    for (int r = 0; r < 4; ++r) {
+        if ((old >> sh) & 0xffffu) return false;
+        const u32 got = atomicCAS(word, old, old | ((u32)(s + 1) << sh));
+        if (got == old) return true;
+        old = got;
+    }
+    return false;
+}
+
 // Look up (and insert if absent) node v for every active lane.  Warp-collective.
-__device__ int lookup_insert(const State &st, Unit &U, i32 v, bool active, const i64 *kglob) {
+template <class VT, class HT, bool WEIGHTED>
+__device__ int lookup_insert(const State<VT, HT, WEIGHTED> &st, const DevGraph &G, Unit &U, i32 v, bool active) {
     const u32 hm = (u32)st.H - 1u;
     int slot = -1;
     u32 h = 0;
@@ -99,7 +164,7 @@ __device__ int lookup_insert(const State &st, Unit &U, i32 v, bool active, const
         h = hash_node(v) & hm;
         int p = 0;
         for (; p < st.H; ++p) {
-            u32 x = st.hsh[h];
+            const u32 x = st.hsh[h];
             if (x == 0u) {
                 need = true;
                 break;
@@ -124,16 +189,12 @@ __device__ int lookup_insert(const State &st, Unit &U, i32 v, bool active, const
             slot = U.ns + __popc(ball & lanemask_lt());
             st.id[slot] = v;
             st.din[slot] = 0;
-            st.kdeg[slot] = kglob[v];
+            st.kdeg[slot] = (VT)G.k[v];
             st.key[slot] = NEG_INF;
             st.flag[slot] = 0;
-            st.hpos[slot] = -1;
             int p = 0;
             for (; p < st.H; ++p) {
-                if (atomicCAS(&st.hsh[h], 0u, (u32)(slot + 1)) == 0u) {
-                    st.hpos[slot] = (i32)h;
-                    break;
-                }
+                if (claim_bucket(st.hsh, h, slot)) break;
                 h = (h + 1u) & hm;
             }
             if (p == st.H) U.err = true;
@@ -145,28 +206,31 @@ __device__ int lookup_insert(const State &st, Unit &U, i32 v, bool active, const
     return slot;
 }
 
-__device__ __forceinline__ double prio_key(i64 d, double logk, double alpha) {
-    return log((double)d) - alpha * logk;
+__device__ __forceinline__ float rank_key(i64 d, i64 k, float alpha32) {
+    return logf((float)d) - alpha32 * logf((float)k);
 }
 
-// Slot a ranks before slot b in the queue (exact; canonical argument order so
-// that every lane evaluating the pair gets the same answer).
-__device__ __forceinline__ bool ranks_before(const State &st, int a, double ka, int b, double kb, Unit &U) {
-    const double diff = ka - kb;
+// Slot a ranks before slot b (exact; canonical argument order so that every
+// lane evaluating the pair gets the same answer).
+template <class S>
+__device__ __forceinline__ bool ranks_before(const S &st, int a, float ka, int b, float kb, Unit &U) {
+    const float diff = ka - kb;
     if (diff > U.E2) return true;
     if (diff < -U.E2) return false;
     const bool swap = a > b;
     const int x = swap ? b : a, y = swap ? a : b;
-    int s = exact::sign_delta(st.din[x], st.din[y], st.kdeg[x], st.kdeg[y], U.alpha, &U.xflags);
-    bool xfirst = s ? (s > 0) : (st.id[x] < st.id[y]);
+    const int s = exact::sign_delta((i64)st.din[x], (i64)st.din[y], (i64)st.kdeg[x], (i64)st.kdeg[y], U.alpha,
+                                    &U.xflags);
+    const bool xfirst = s ? (s > 0) : (st.id[x] < st.id[y]);
     return swap ? !xfirst : xfirst;
 }
 
-__device__ __forceinline__ void warp_best(const State &st, int &best, double &bk, Unit &U) {
+template <class S>
+__device__ __forceinline__ void warp_best(const S &st, int &best, float &bk, Unit &U) {
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
-        int ob = __shfl_xor_sync(FULL_MASK, best, off);
-        double ok = __shfl_xor_sync(FULL_MASK, bk, off);
+        const int ob = __shfl_xor_sync(FULL_MASK, best, off);
+        const float ok = __shfl_xor_sync(FULL_MASK, bk, off);
         if (ob >= 0 && (best < 0 || ranks_before(st, ob, ok, best, bk, U))) {
             best = ob;
             bk = ok;
@@ -176,59 +240,154 @@ __device__ __forceinline__ void warp_best(const State &st, int &best, double &bk
     bk = __shfl_sync(FULL_MASK, bk, 0);
 }
 
-// Highest-ranked queued slot, or -1.
-__device__ int queue_top(const State &st, Unit &U) {
+constexpr int UNROLL = 4;
+
+// Exact argmax over every queued slot (one pass).
+template <class S>
+__device__ int queue_top_flat(const S &st, Unit &U) {
     const int lane = threadIdx.x & 31;
     int best = -1;
-    double bk = NEG_INF;
-    for (int i = lane; i < U.ns; i += 32) {
-        const double k = st.key[i];
-        if (k == NEG_INF) continue;
-        if (best < 0 || ranks_before(st, i, k, best, bk, U)) {
-            best = i;
-            bk = k;
+    float bk = NEG_INF;
+    for (int b = 0; b < U.ns; b += 32 * UNROLL) {
+        float kv[UNROLL];
+#pragma unroll
+        for (int j = 0; j < UNROLL; ++j) {
+            const int i = b + 32 * j + lane;
+            kv[j] = i < U.ns ? st.key[i] : NEG_INF;
+        }
+#pragma unroll
+        for (int j = 0; j < UNROLL; ++j) {
+            if (kv[j] == NEG_INF) continue;
+            const int i = b + 32 * j + lane;
+            if (best < 0 || ranks_before(st, i, kv[j], best, bk, U)) {
+                best = i;
+                bk = kv[j];
+            }
         }
     }
     warp_best(st, best, bk, U);
     return best;
+}
+
+template <class S>
+__device__ __forceinline__ int max_bound(const S &st, int G) {
+    int m = ORD_NEG_INF;
+    for (int g = threadIdx.x & 31; g < G; g += 32) m = max(m, st.gmax[g]);
+    return __reduce_max_sync(FULL_MASK, m);
+}
+
+template <class S>
+__device__ void rebuild_groups(const S &st, const Unit &U) {
+    const int lane = threadIdx.x & 31;
+    const int G = (U.ns + 31) >> 5;
+    for (int g = 0; g < G; ++g) {
+        const int i = g * 32 + lane;
+        const int o = __reduce_max_sync(FULL_MASK, i < U.ns ? ord(st.key[i]) : ORD_NEG_INF);
+        if (lane == 0) st.gmax[g] = o;
+    }
+    for (int g = G + lane; g < st.C / 32; g += 32) st.gmax[g] = ORD_NEG_INF;
+    __syncwarp();
+}
+
+template <class S>
+__device__ int queue_top(const S &st, Unit &U) {
+    const int G = (U.ns + 31) >> 5;
+    if (G <= 8) return queue_top_flat(st, U);
+    const int lane = threadIdx.x & 31;
+    int best = -1;
+    float bk = NEG_INF;
+    int M = max_bound(st, G);
+    for (int iter = 0; iter < 64; ++iter) {
+        if (M == ORD_NEG_INF) return best;
+        const int othr = ord(unord(M) - 2.0f * U.E2);
+        for (int base = 0; base < G; base += 32) {
+            const int g = base + lane;
+            u32 ball = __ballot_sync(FULL_MASK, g < G && st.gmax[g] >= othr);
+            while (ball) {
+                const int gg = base + __ffs(ball) - 1;
+                ball &= ball - 1;
+                const int i = gg * 32 + lane;
+                const float k = i < U.ns ? st.key[i] : NEG_INF;
+                int lb = k == NEG_INF ? -1 : i;
+                float lk = k;
+                warp_best(st, lb, lk, U);
+                if (lane == 0) st.gmax[gg] = lb >= 0 ? ord(lk) : ORD_NEG_INF;
+                if (lb >= 0 && (best < 0 || ranks_before(st, lb, lk, best, bk, U))) {
+                    best = lb;
+                    bk = lk;
+                }
+            }
+        }
+        __syncwarp();
+        const int M2 = max_bound(st, G);
+        if (M2 == M) return best;
+        M = M2;
+    }
+    return queue_top_flat(st, U);
 }
 
 // Highest-ranked queued slot that passes the add test at the current K, V.
-__device__ int best_passing(const State &st, Unit &U) {
+template <class S>
+__device__ int best_passing(const S &st, Unit &U) {
     const int lane = threadIdx.x & 31;
     int best = -1;
-    double bk = NEG_INF;
-    for (int i = lane; i < U.ns; i += 32) {
-        const double k = st.key[i];
-        if (k == NEG_INF) continue;
-        const i64 d = st.din[i], kd = st.kdeg[i];
-        if (!exact::add_possible(U.K, U.V, d, kd, U.alpha)) continue;
-        if (!exact::add_test(U.K, U.V, d, kd, U.alpha, &U.xflags)) continue;
-        if (best < 0 || ranks_before(st, i, k, best, bk, U)) {
-            best = i;
-            bk = k;
+    float bk = NEG_INF;
+    for (int b = 0; b < U.ns; b += 32 * UNROLL) {
+        float kv[UNROLL];
+#pragma unroll
+        for (int j = 0; j < UNROLL; ++j) {
+            const int i = b + 32 * j + lane;
+            kv[j] = i < U.ns ? st.key[i] : NEG_INF;
+        }
+#pragma unroll
+        for (int j = 0; j < UNROLL; ++j) {
+            if (kv[j] == NEG_INF) continue;
+            const int i = b + 32 * j + lane;
+            const i64 d = st.din[i], kd = st.kdeg[i];
+            if (!exact::add_possible(U.K, U.V, d, kd, U.alpha32)) continue;
+            if (!exact::add_test(U.K, U.V, d, kd, U.alpha, U.alpha32, &U.xflags)) continue;
+            if (best < 0 || ranks_before(st, i, kv[j], best, bk, U)) {
+                best = i;
+                bk = kv[j];
+            }
         }
     }
     warp_best(st, best, bk, U);
     return best;
 }
 
-// Pop (reject) every queued slot ranked before `best` (all of them if best < 0).
-__device__ void drop_before(const State &st, int best, Unit &U) {
+// Pop (reject) every queued slot ranked before `best` (all of them if best
+// < 0), then recompute every group best.
+template <class S>
+__device__ void drop_before(const S &st, int best, Unit &U) {
     const int lane = threadIdx.x & 31;
-    const double bk = best >= 0 ? st.key[best] : 0.0;
-    for (int i = lane; i < U.ns; i += 32) {
-        const double k = st.key[i];
-        if (k == NEG_INF) continue;
-        if (best < 0 || ranks_before(st, i, k, best, bk, U)) st.key[i] = NEG_INF;
+    const float bk = best >= 0 ? st.key[best] : 0.0f;
+    for (int b = 0; b < U.ns; b += 32 * UNROLL) {
+        float kv[UNROLL];
+#pragma unroll
+        for (int j = 0; j < UNROLL; ++j) {
+            const int i = b + 32 * j + lane;
+            kv[j] = i < U.ns ? st.key[i] : NEG_INF;
+        }
+#pragma unroll
+        for (int j = 0; j < UNROLL; ++j) {
+            if (kv[j] == NEG_INF) continue;
+            const int i = b + 32 * j + lane;
+            if (best < 0 || ranks_before(st, i, kv[j], best, bk, U)) st.key[i] = NEG_INF;
+        }
     }
     __syncwarp();
 }
 
-// Scan node u's row, adding sign*w to d_in of every neighbour; with requeue,
-// (re)insert outside neighbours in the queue with their new key.
-__device__ void expand(const State &st, const DevGraph &G, Unit &U, i32 u, int sign, bool requeue) {
+// Scan the row of the node in `slot`, adding sign*w to d_in of every
+// neighbour; with requeue, (re)insert outside neighbours in the queue with
+// their new key and fold them into their group's best.
+template <class VT, class HT, bool WEIGHTED>
+__device__ void expand(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Unit &U, int slot, int sign,
+                       bool requeue) {
+    const DevGraph &G = a.G;
     const int lane = threadIdx.x & 31;
+    const i32 u = st.id[slot];
     const i64 rs = G.rp[u], re = G.rp[u + 1];
     for (i64 b = rs; b < re; b += 32) {
         const i64 e = b + lane;
@@ -237,23 +396,30 @@ __device__ void expand(const State &st, const DevGraph &G, Unit &U, i32 u, int s
         i64 w = 0;
         if (act) {
             v = G.col[e];
-            w = G.wfx ? G.wfx[e] : 1;
+            w = WEIGHTED ? G.wfx[e] : 1;
         }
-        const int s = lookup_insert(st, U, v, act, G.k);
+        const int s = lookup_insert(st, G, U, v, act);
         if (U.ovf || U.err) return;
+        bool upd = false;
+        float k = NEG_INF;
         if (act) {
-            const i64 d = st.din[s] + sign * w;
-            st.din[s] = d;
-            if (requeue && !(st.flag[s] & F_MEMBER)) st.key[s] = prio_key(d, G.logk[v], U.alpha);
+            const i64 d = (i64)st.din[s] + sign * w;
+            st.din[s] = (VT)d;
+            if (requeue && !(st.flag[s] & F_MEMBER)) {
+                k = rank_key(d, (i64)st.kdeg[s], U.alpha32);
+                st.key[s] = k;
+                upd = true;
+            }
         }
+        if (upd) atomicMax(&st.gmax[s >> 5], ord(k));
     }
     __syncwarp();
     U.edges += re - rs;
 }
 
-__device__ void accept(const State &st, const DevGraph &G, Unit &U, int s) {
+template <class VT, class HT, bool WEIGHTED>
+__device__ void accept(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Unit &U, int s) {
     const i64 d = st.din[s], kd = st.kdeg[s];
-    const i32 u = st.id[s];
     __syncwarp();
     if ((threadIdx.x & 31) == 0) {
         st.flag[s] |= F_MEMBER;
@@ -263,11 +429,12 @@ __device__ void accept(const State &st, const DevGraph &G, Unit &U, int s) {
     U.K += 2 * d;
     U.V += kd;
     U.adds++;
-    expand(st, G, U, u, +1, true);
+    expand(st, a, U, s, +1, true);
 }
 
 // Smallest-id member (not the seed, id > last) whose removal raises f; -1 if none.
-__device__ int first_removable(const State &st, Unit &U, i32 last) {
+template <class S>
+__device__ int first_removable(const S &st, Unit &U, i32 last) {
     const int lane = threadIdx.x & 31;
     i32 bid = INT32_MAX;
     int bslot = -1;
@@ -276,8 +443,8 @@ __device__ int first_removable(const State &st, Unit &U, i32 last) {
         const i32 u = st.id[i];
         if (u == U.seed || u <= last || u >= bid) continue;
         const i64 d = st.din[i], kd = st.kdeg[i];
-        if (!exact::remove_possible(U.K, U.V, d, kd, U.alpha)) continue;
-        if (!exact::remove_test(U.K, U.V, d, kd, U.alpha, &U.xflags)) continue;
+        if (!exact::remove_possible(U.K, U.V, d, kd, U.alpha32)) continue;
+        if (!exact::remove_test(U.K, U.V, d, kd, U.alpha, U.alpha32, &U.xflags)) continue;
         bid = u;
         bslot = i;
     }
@@ -287,32 +454,49 @@ __device__ int first_removable(const State &st, Unit &U, i32 last) {
     return __shfl_sync(FULL_MASK, bslot, __ffs(who) - 1);
 }
 
-__device__ void remove_node(const State &st, const DevGraph &G, Unit &U, int s) {
+template <class VT, class HT, bool WEIGHTED>
+__device__ void remove_node(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Unit &U, int s) {
     const i64 d = st.din[s], kd = st.kdeg[s];
-    const i32 u = st.id[s];
     __syncwarp();
-    if ((threadIdx.x & 31) == 0) st.flag[s] &= ~F_MEMBER;
+    if ((threadIdx.x & 31) == 0) st.flag[s] &= (unsigned char)~F_MEMBER;
     __syncwarp();
     U.K -= 2 * d;
     U.V -= kd;
     U.removes++;
-    expand(st, G, U, u, -1, false);
+    expand(st, a, U, s, -1, false);
 }
 
-__device__ void clear_hash(const State &st, const Unit &U) {
+// Empty the hash table for the next unit: first find every slot's bucket
+// (into the key array, no longer needed), then zero them.
+template <class S>
+__device__ void clear_hash(const S &st, const Unit &U) {
+    const int lane = threadIdx.x & 31;
     __syncwarp();
-    if (U.err) {
-        for (int i = threadIdx.x & 31; i < st.H; i += 32) st.hsh[i] = 0u;
+    if (U.err || 4 * U.ns >= st.H) {
+        for (int i = lane; i < st.H; i += 32) st.hsh[i] = 0;
     } else {
-        for (int i = threadIdx.x & 31; i < U.ns; i += 32)
-            if (st.hpos[i] >= 0) st.hsh[st.hpos[i]] = 0u;
+        const u32 hm = (u32)st.H - 1u;
+        i32 *pos = (i32 *)st.key;
+        for (int i = lane; i < U.ns; i += 32) {
+            u32 h = hash_node(st.id[i]) & hm;
+            int p = 0;
+            while ((u32)st.hsh[h] != (u32)(i + 1) && p < st.H) {
+                h = (h + 1u) & hm;
+                ++p;
+            }
+            pos[i] = p < st.H ? (i32)h : -1;
+        }
+        __syncwarp();
+        for (int i = lane; i < U.ns; i += 32)
+            if (pos[i] >= 0) st.hsh[pos[i]] = 0;
     }
     __syncwarp();
 }
 
-// Sort the members ascending into scratch (the key array viewed as int32[2C]),
+// Sort the members ascending into scratch (the key array viewed as int32[C]),
 // hash the list and write it out.  Returns false if the output buffer is full.
-__device__ bool emit(const State &st, const GrowArgs &a, const DevGraph &G, Unit &U, i64 unit, int status) {
+template <class S>
+__device__ bool emit(const S &st, const GrowArgs &a, Unit &U, i64 unit, int status) {
     const int lane = threadIdx.x & 31;
     i32 *scr = (i32 *)st.key;
     int m = 0;
@@ -321,7 +505,7 @@ __device__ bool emit(const State &st, const GrowArgs &a, const DevGraph &G, Unit
         const int i = b + lane;
         const bool mem = i < U.ns && (st.flag[i] & F_MEMBER);
         const u32 ball = __ballot_sync(FULL_MASK, mem);
-        i32 v = mem ? st.id[i] : 0;
+        const i32 v = mem ? st.id[i] : 0;
         __syncwarp();
         if (mem) scr[m + __popc(ball & lanemask_lt())] = v;
         m += __popc(ball);
@@ -367,7 +551,7 @@ __device__ bool emit(const State &st, const GrowArgs &a, const DevGraph &G, Unit
         double f = 0.0;
         if (U.K > 0) {
             const double LN2 = 0.6931471805599453;
-            f = exp(log((double)U.K) - U.alpha * log((double)U.V) + (1.0 - U.alpha) * (double)G.unit_exp * LN2);
+            f = exp(log((double)U.K) - U.alpha * log((double)U.V) + (1.0 - U.alpha) * (double)a.G.unit_exp * LN2);
         }
         a.uf[unit] = f;
         i64 *stt = a.ustat + unit * MSCD_NSTATS;
@@ -384,14 +568,16 @@ __device__ bool emit(const State &st, const GrowArgs &a, const DevGraph &G, Unit
     return true;
 }
 
-__device__ void grow_unit(const State &st, const GrowArgs &a, i64 unit) {
+template <class VT, class HT, bool WEIGHTED>
+__device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, i64 unit) {
     const int lane = threadIdx.x & 31;
     const DevGraph &G = a.G;
     Unit U;
     const i64 si = unit % a.n_seeds;
     U.alpha = a.alphas[unit / a.n_seeds];
+    U.alpha32 = (float)U.alpha;
     U.seed = a.seeds ? a.seeds[si] : (i32)si;
-    U.E2 = 2.0 * 0x1p-44 * (1.0 + U.alpha);
+    U.E2 = 2.0f * 0x1p-20f * (1.0f + U.alpha32) * (1.0f + a.log_kmax);
     U.K = 0;
     U.V = G.k[U.seed];
     U.ns = 0;
@@ -400,10 +586,10 @@ __device__ void grow_unit(const State &st, const GrowArgs &a, i64 unit) {
     U.ovf = U.err = false;
     int status = MSCD_OK;
 
-    lookup_insert(st, U, U.seed, lane == 0, G.k);  // slot 0
+    lookup_insert(st, G, U, U.seed, lane == 0);  // slot 0
     if (lane == 0) st.flag[0] = F_MEMBER;
     __syncwarp();
-    expand(st, G, U, U.seed, +1, false);
+    expand(st, a, U, 0, +1, false);
 
     while (!U.ovf && !U.err) {
         if (U.rounds >= a.max_rounds) {
@@ -414,20 +600,22 @@ __device__ void grow_unit(const State &st, const GrowArgs &a, i64 unit) {
         // queue = whole frontier
         for (int i = lane; i < U.ns; i += 32) {
             const i64 d = st.din[i];
-            st.key[i] = (!(st.flag[i] & F_MEMBER) && d > 0) ? prio_key(d, G.logk[st.id[i]], U.alpha) : NEG_INF;
+            st.key[i] =
+                (!(st.flag[i] & F_MEMBER) && d > 0) ? rank_key(d, (i64)st.kdeg[i], U.alpha32) : NEG_INF;
         }
         __syncwarp();
+        rebuild_groups(st, U);
         i64 added = 0;
         for (;;) {
             const int top = queue_top(st, U);
             if (top < 0) break;
             int s = top;
-            if (!exact::add_test(U.K, U.V, st.din[top], st.kdeg[top], U.alpha, &U.xflags)) {
+            if (!exact::add_test(U.K, U.V, (i64)st.din[top], (i64)st.kdeg[top], U.alpha, U.alpha32, &U.xflags)) {
                 s = best_passing(st, U);
                 drop_before(st, s, U);
                 if (s < 0) break;
             }
-            accept(st, G, U, s);
+            accept(st, a, U, s);
             added++;
             if (U.ovf || U.err) break;
         }
@@ -439,7 +627,7 @@ __device__ void grow_unit(const State &st, const GrowArgs &a, i64 unit) {
                 const int s = first_removable(st, U, last);
                 if (s < 0) break;
                 last = st.id[s];
-                remove_node(st, G, U, s);
+                remove_node(st, a, U, s);
                 removed++;
                 if (U.ovf || U.err) break;
             }
@@ -453,20 +641,24 @@ __device__ void grow_unit(const State &st, const GrowArgs &a, i64 unit) {
         if (lane == 0) a.retry_state[atomicAdd(a.n_retry_state, 1ull)] = unit;
     } else {
         if (status == MSCD_OK && (U.xflags & EXACT_UNDECIDED)) status = MSCD_EUNDECIDED;
-        if (!emit(st, a, G, U, unit, status)) {
+        if (!emit(st, a, U, unit, status)) {
             if (lane == 0) a.retry_out[atomicAdd(a.n_retry_out, 1ull)] = unit;
         }
     }
     clear_hash(st, U);
 }
 
+// One unit per warp, persistent: units are taken from a global counter until
+// the work list is exhausted.  State: dynamic shared memory (warp w of the
+// CTA at w * state_bytes) or the global arena (warp at its global index).
+template <class VT, class HT, bool WEIGHTED>
 __global__ void __launch_bounds__(GROW_MAX_THREADS) grow_kernel(GrowArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const i64 gw = (i64)blockIdx.x * (blockDim.x >> 5) + wib;
     unsigned char *base = a.use_smem ? smem + (size_t)wib * a.state_bytes : a.gstate + (size_t)gw * a.state_bytes;
-    const State st = carve(base, a.cap);
-    for (int i = lane; i < st.H; i += 32) st.hsh[i] = 0u;
+    const State<VT, HT, WEIGHTED> st = carve<VT, HT, WEIGHTED>(base, a.cap);
+    for (int i = lane; i < st.H; i += 32) st.hsh[i] = 0;
     __syncwarp();
     for (;;) {
         unsigned long long t = 0;
@@ -478,23 +670,52 @@ __global__ void __launch_bounds__(GROW_MAX_THREADS) grow_kernel(GrowArgs a) {
     }
 }
 
-}  // namespace
-
-size_t grow_state_bytes(int cap) { return 41ull * (size_t)cap; }
-
-int grow_launch(const GrowArgs &a, int blocks, int threads, size_t smem, cudaStream_t st) {
+template <class VT, class HT, bool WEIGHTED>
+int launch_t(const GrowArgs &a, int blocks, int threads, size_t smem, cudaStream_t st, int *occ) {
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(grow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(grow_kernel<VT, HT, WEIGHTED>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_status(e);
     }
-    grow_kernel<<<blocks, threads, smem, st>>>(a);
+    if (occ)
+        return cuda_status(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, grow_kernel<VT, HT, WEIGHTED>, threads, smem));
+    grow_kernel<VT, HT, WEIGHTED><<<blocks, threads, smem, st>>>(a);
+    note_launch();
     return cuda_status(cudaGetLastError());
 }
 
-int grow_occupancy(int threads, size_t smem, int *blocks_per_sm) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(grow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_status(e);
-    }
-    return cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, grow_kernel, threads, smem));
+typedef unsigned short u16;
+
+// Dispatch on the slot value type (16-bit when every degree fits, else 32 /
+// 64-bit) and the bucket type (16-bit up to 32768 slots).
+int dispatch(const GrowArgs &a, int blocks, int threads, size_t smem, cudaStream_t st, int *occ) {
+    const bool w = a.G.wfx != nullptr;
+    const bool small_deg = !w && a.G.kmax < 65536;
+    const bool h16 = a.cap <= 32768;
+    if (w) return h16 ? launch_t<i64, u16, true>(a, blocks, threads, smem, st, occ)
+                      : launch_t<i64, u32, true>(a, blocks, threads, smem, st, occ);
+    if (small_deg) return h16 ? launch_t<u16, u16, false>(a, blocks, threads, smem, st, occ)
+                              : launch_t<u16, u32, false>(a, blocks, threads, smem, st, occ);
+    return h16 ? launch_t<i32, u16, false>(a, blocks, threads, smem, st, occ)
+               : launch_t<i32, u32, false>(a, blocks, threads, smem, st, occ);
+}
+
+}  // namespace
+
+size_t grow_state_bytes(const DevGraph &G, int cap) {
+    const bool w = G.wfx != nullptr;
+    const bool h16 = cap <= 32768;
+    if (w) return h16 ? state_bytes_t<i64, u16, true>(cap) : state_bytes_t<i64, u32, true>(cap);
+    if (G.kmax < 65536)
+        return h16 ? state_bytes_t<u16, u16, false>(cap) : state_bytes_t<u16, u32, false>(cap);
+    return h16 ? state_bytes_t<i32, u16, false>(cap) : state_bytes_t<i32, u32, false>(cap);
+}
+
+int grow_launch(const GrowArgs &a, int blocks, int threads, size_t smem, cudaStream_t st) {
+    return dispatch(a, blocks, threads, smem, st, nullptr);
+}
+
+int grow_occupancy(const GrowArgs &a, int threads, size_t smem, int *blocks_per_sm) {
+    return dispatch(a, 0, threads, smem, nullptr, blocks_per_sm);
 }

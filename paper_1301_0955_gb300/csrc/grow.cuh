@@ -15,11 +15,12 @@ struct GrowArgs {
     i64 n_work;
     unsigned long long *work_counter;
     // per-warp node-slot state
-    int cap;                // slots per warp (power of 2)
+    int cap;                // node slots per unit (power of 2, >= 32)
     int use_smem;           // 1: dynamic shared memory, 0: global arena
     unsigned char *gstate;  // global arena (warps * state_bytes)
-    size_t state_bytes;
+    size_t state_bytes;     // per warp
     i64 max_rounds;
+    float log_kmax;         // log of the largest degree (bounds the binary32 key error)
     // outputs (unit-indexed)
     i32 *out_nodes;
     unsigned long long *out_cursor;
@@ -39,6 +40,8 @@ struct GrowArgs {
     u32 *error_flags;
 };
 
-size_t grow_state_bytes(int cap);
+// Bytes of one unit's state at `cap` node slots on graph G.
+size_t grow_state_bytes(const DevGraph &G, int cap);
+// One unit per warp; `threads` = 32 * warps per CTA.
 int grow_launch(const GrowArgs &a, int blocks, int threads, size_t smem, cudaStream_t st);
-int grow_occupancy(int threads, size_t smem, int *blocks_per_sm);
+int grow_occupancy(const GrowArgs &a, int threads, size_t smem, int *blocks_per_sm);

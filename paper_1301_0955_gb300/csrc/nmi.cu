@@ -10,13 +10,24 @@
 //   H(X|Y)     = mean_k H(X_k|Y) / H(X_k)   (0 for a community of all n nodes)
 //   N          = 1 - [H(X|Y) + H(Y|X)] / 2
 //
-// Only two kinds of pair can be admitted, so only they are evaluated:
-//   * pairs that share a node (counted through the node -> communities map);
-//   * disjoint pairs with |X_k| + |Y_l| > n/2.  For a disjoint pair with
-//     s = (|X_k| + |Y_l|)/n <= 1/2: h(P00) = h(1-s) <= h(s) (h(1-s) <= h(s)
+// Shortcut: when X_k has an identical partner Y_l (equal sorted lists), the
+// candidate of that pair is exactly 0 (H(X_k, Y_l) = H(Y_l)), and no
+// candidate is negative, so H(X_k|Y) = 0 without counting; likewise for Y_l.
+// Successive scales share most communities, so most of the work goes.
+//
+// For the other communities, only two kinds of partner can be admitted:
+//   * partners that share a node;
+//   * disjoint partners with |A| + |B| > n/2.  For a disjoint pair with
+//     s = (|A| + |B|)/n <= 1/2: h(P00) = h(1-s) <= h(s) (h(1-s) <= h(s)
 //     on [0, 1/2]) <= h(P10) + h(P01) (h concave with h(0) = 0 is
 //     subadditive), and h(P11) = 0, so the admission test fails.
-// Per-k results are reduced in a fixed order, so the value is deterministic.
+// The intersections of the sharing pairs are counted by a warp per community:
+// it walks its members' lists of partner communities (the lanes spread over
+// one list at a time, whose entries are distinct) and counts in a
+// shared-memory hash; a community that meets too many partners is redone
+// with a global-memory table of its own.  Minima are kept as the bits of
+// non-negative doubles; per-community terms are summed in a fixed order, so
+// the value is deterministic.
 #include <algorithm>
 #include <vector>
 
@@ -25,20 +36,30 @@
 
 namespace {
 
+constexpr int NMI_WARPS = 8;
+constexpr int NMI_TABLE = 1024;  // shared-memory hash entries per warp
+
 __device__ __forceinline__ double hterm(i64 c, double inv_n) {
     if (c <= 0) return 0.0;
     const double p = (double)c * inv_n;
     return -p * log2(p);
 }
 
-// Candidate H(X_k|Y_l) if admitted, else +inf.
-__device__ __forceinline__ double cond_candidate(i64 n11, i64 sx, i64 sy, i64 n, double inv_n) {
-    const i64 n10 = sx - n11, n01 = sy - n11, n00 = n - n11 - n10 - n01;
+// Candidate H(A|B) for two communities of sizes sa, sb sharing n11 nodes, if
+// admitted; else +inf.
+__device__ __forceinline__ double cond_candidate(i64 n11, i64 sa, i64 sb, i64 n, double inv_n) {
+    const i64 n10 = sa - n11, n01 = sb - n11, n00 = n - n11 - n10 - n01;
     const i64 lo1 = min(n11, n00), hi1 = max(n11, n00), lo2 = min(n01, n10), hi2 = max(n01, n10);
     if (lo1 == lo2 && hi1 == hi2) return __builtin_huge_val();
     const double h11 = hterm(n11, inv_n), h00 = hterm(n00, inv_n), h01 = hterm(n01, inv_n), h10 = hterm(n10, inv_n);
     if (!(h11 + h00 > h01 + h10)) return __builtin_huge_val();
-    return (h11 + h10 + h01 + h00) - (hterm(sy, inv_n) + hterm(n - sy, inv_n));
+    return (h11 + h10 + h01 + h00) - (hterm(sb, inv_n) + hterm(n - sb, inv_n));
+}
+
+__device__ __forceinline__ double entropy(i64 s, i64 n, double inv_n) { return hterm(s, inv_n) + hterm(n - s, inv_n); }
+
+__device__ __forceinline__ unsigned long long min_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v > 0.0 ? v : 0.0);
 }
 
 __global__ void count_memberships(const i32 *nodes, i64 m, i32 *cnt) {
@@ -50,7 +71,7 @@ __global__ void widen_i32(const i32 *a, i64 n, i64 *b) {
     for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) b[i] = a[i];
 }
 
-// Warp per community l of Y: append l to the list of each member.
+// Warp per community l: append l to the list of each member.
 __global__ void fill_memberships(const i64 *cptr, const i32 *nodes, i64 C, const i64 *mptr, i32 *cursor, i32 *mlist) {
     const int lane = threadIdx.x & 31;
     const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
@@ -61,44 +82,171 @@ __global__ void fill_memberships(const i64 *cptr, const i32 *nodes, i64 C, const
         }
 }
 
-// Warp per community k of X: table size for the communities of Y it meets.
-__global__ void table_sizes(const i64 *xptr, const i32 *xnodes, i64 CX, const i32 *ycnt, i64 CY, i64 *tsz) {
+// Hash table of community list hashes (0 = empty bucket; list hashes are never 0).
+__global__ void hash_insert(const u64 *chash, i64 C, u64 *tkey, i32 *tval, i64 tmask) {
+    for (i64 l = (i64)blockIdx.x * blockDim.x + threadIdx.x; l < C; l += (i64)gridDim.x * blockDim.x) {
+        i64 h = (i64)(chash[l] & (u64)tmask);
+        for (i64 p = 0; p <= tmask; ++p) {
+            if (atomicCAS((unsigned long long *)&tkey[h], 0ull, (unsigned long long)chash[l]) == 0ull) {
+                tval[h] = (i32)l;
+                break;
+            }
+            h = (h + 1) & tmask;
+        }
+    }
+}
+
+// Warp per X_k: an identical Y_l (same hash, same list) zeroes both.
+__global__ void match_identical(const i64 *xptr, const i32 *xnodes, const u64 *xhash, i64 CX, const i64 *yptr,
+                                const i32 *ynodes, const u64 *tkey, const i32 *tval, i64 tmask,
+                                unsigned char *zeroX, unsigned char *zeroY) {
     const int lane = threadIdx.x & 31;
     const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
     for (i64 k = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < CX; k += warps) {
-        i64 s = 0;
-        for (i64 e = xptr[k] + lane; e < xptr[k + 1]; e += 32) s += ycnt[xnodes[e]];
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
-        s = min(s, CY);
-        i64 t = 2;
-        while (t < 2 * s) t <<= 1;
-        if (lane == 0) tsz[k] = t;
+        const u64 key = xhash[k];
+        const i64 sx = xptr[k + 1] - xptr[k];
+        i64 h = (i64)(key & (u64)tmask);
+        for (i64 p = 0; p <= tmask; ++p) {
+            const u64 tk = tkey[h];
+            if (tk == 0ull) break;
+            if (tk == key) {
+                const i32 l = tval[h];
+                bool eq = yptr[l + 1] - yptr[l] == sx;
+                if (eq) {
+                    const i32 *a = xnodes + xptr[k], *b = ynodes + yptr[l];
+                    bool diff = false;
+                    for (i64 i = lane; i < sx; i += 32) diff |= a[i] != b[i];
+                    eq = !__any_sync(FULL_MASK, diff);
+                }
+                if (eq) {
+                    if (lane == 0) {
+                        zeroX[k] = 1;
+                        zeroY[l] = 1;
+                    }
+                    break;
+                }
+            }
+            h = (h + 1) & tmask;
+        }
+    }
+}
+
+// Initial minima: 0 for communities with an identical partner, else H(C)
+// (the value when no partner is admitted); list the others.
+__global__ void init_best(const i64 *ptr, i64 C, i64 n, const unsigned char *zero, unsigned long long *best,
+                          i32 *active, unsigned long long *n_active) {
+    const double inv_n = 1.0 / (double)n;
+    for (i64 l = (i64)blockIdx.x * blockDim.x + threadIdx.x; l < C; l += (i64)gridDim.x * blockDim.x) {
+        if (zero[l]) {
+            best[l] = 0ull;
+        } else {
+            best[l] = min_bits(entropy(ptr[l + 1] - ptr[l], n, inv_n));
+            active[atomicAdd(n_active, 1ull)] = (i32)l;
+        }
     }
 }
 
 __device__ __forceinline__ u32 hash_comm(i32 l) { return (u32)l * 0x9E3779B1u; }
 
-// Warp per community k of X: intersections with every Y_l it meets, then
-// the minimum admitted conditional entropy, normalised.
-__global__ void cond_entropy(const i64 *xptr, const i32 *xnodes, i64 CX, const i64 *yptr, i64 CY, const i64 *mptr,
-                             const i32 *mlist, const i64 *toff, i32 *tkey, i32 *tcnt, const i32 *big, i64 nbig, i64 n,
-                             double *term) {
+struct DirArgs {
+    const i64 *aptr;
+    const i32 *anodes;
+    const i32 *active;  // communities of A to process
+    i64 n_active;
+    const i64 *bptr;
+    const i64 *mptr;    // node -> communities of B
+    const i32 *mlist;
+    i64 n;
+    unsigned long long *best;  // per A community (bits of doubles)
+    i64 *spill;                // positions in `active` redone with global tables
+    unsigned long long *n_spill;
+    const i64 *toff;
+    i32 *tkey, *tcnt;
+};
+
+// Warp per active A community: intersections with every B community it meets
+// (shared-memory hash), minimum admitted candidate.
+__global__ void __launch_bounds__(NMI_WARPS * 32) pairs_smem(DirArgs a) {
+    __shared__ i32 skey[NMI_WARPS][NMI_TABLE];
+    __shared__ i32 scnt[NMI_WARPS][NMI_TABLE];
+    __shared__ int sfill[NMI_WARPS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const i64 warps = (i64)gridDim.x * NMI_WARPS;
+    const double inv_n = 1.0 / (double)a.n;
+    i32 *keys = skey[w];
+    i32 *cnts = scnt[w];
+    for (i64 q = (i64)blockIdx.x * NMI_WARPS + w; q < a.n_active; q += warps) {
+        const i32 k = a.active[q];
+        for (int t = lane; t < NMI_TABLE; t += 32) {
+            keys[t] = -1;
+            cnts[t] = 0;
+        }
+        if (lane == 0) sfill[w] = 0;
+        __syncwarp();
+        bool over = false;
+        for (i64 e = a.aptr[k]; e < a.aptr[k + 1] && !over; ++e) {
+            const i32 u = a.anodes[e];
+            for (i64 j = a.mptr[u] + lane; j < a.mptr[u + 1]; j += 32) {
+                const i32 l = a.mlist[j];
+                u32 h = hash_comm(l) & (NMI_TABLE - 1);
+                for (int p = 0; p < NMI_TABLE; ++p) {
+                    i32 cur = keys[h];
+                    if (cur == -1) {
+                        cur = atomicCAS(&keys[h], -1, l);
+                        if (cur == -1) {
+                            if (atomicAdd(&sfill[w], 1) >= NMI_TABLE / 2) over = true;
+                            cur = l;
+                        }
+                    }
+                    if (cur == l) {
+                        atomicAdd(&cnts[h], 1);
+                        break;
+                    }
+                    h = (h + 1u) & (NMI_TABLE - 1);
+                }
+            }
+            over = __any_sync(FULL_MASK, over);
+        }
+        if (over) {
+            if (lane == 0) a.spill[atomicAdd(a.n_spill, 1ull)] = q;
+            __syncwarp();
+            continue;
+        }
+        __syncwarp();
+        const i64 sa = a.aptr[k + 1] - a.aptr[k];
+        double bx = __longlong_as_double((long long)a.best[k]);
+        for (int t = lane; t < NMI_TABLE; t += 32) {
+            const i32 l = keys[t];
+            if (l >= 0) bx = min(bx, cond_candidate(cnts[t], sa, a.bptr[l + 1] - a.bptr[l], a.n, inv_n));
+        }
+        for (int o = 16; o; o >>= 1) bx = min(bx, __shfl_xor_sync(FULL_MASK, bx, o));
+        if (lane == 0) a.best[k] = min_bits(bx);
+        __syncwarp();
+    }
+}
+
+// Warp per spilled community: the same with a global table of its own.
+__global__ void pairs_global(DirArgs a, i64 nk) {
     const int lane = threadIdx.x & 31;
     const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
-    const double inv_n = 1.0 / (double)n;
-    for (i64 k = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < CX; k += warps) {
-        const i64 sx = xptr[k + 1] - xptr[k];
-        i32 *keys = tkey + toff[k];
-        i32 *cnts = tcnt + toff[k];
-        const u32 tm = (u32)(toff[k + 1] - toff[k] - 1);
-        for (i64 e = xptr[k] + lane; e < xptr[k + 1]; e += 32) {
-            const i32 u = xnodes[e];
-            for (i64 j = mptr[u]; j < mptr[u + 1]; ++j) {
-                const i32 l = mlist[j];
+    const double inv_n = 1.0 / (double)a.n;
+    for (i64 r = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nk; r += warps) {
+        const i32 k = a.active[a.spill[r]];
+        i32 *keys = a.tkey + a.toff[r];
+        i32 *cnts = a.tcnt + a.toff[r];
+        const u32 tm = (u32)(a.toff[r + 1] - a.toff[r] - 1);
+        for (i64 e = a.aptr[k]; e < a.aptr[k + 1]; ++e) {
+            const i32 u = a.anodes[e];
+            for (i64 j = a.mptr[u] + lane; j < a.mptr[u + 1]; j += 32) {
+                const i32 l = a.mlist[j];
                 u32 h = hash_comm(l) & tm;
                 for (u32 p = 0; p <= tm; ++p) {
-                    const i32 old = atomicCAS(&keys[h], -1, l);
-                    if (old == -1 || old == l) {
+                    i32 cur = keys[h];
+                    if (cur == -1) {
+                        cur = atomicCAS(&keys[h], -1, l);
+                        if (cur == -1) cur = l;
+                    }
+                    if (cur == l) {
                         atomicAdd(&cnts[h], 1);
                         break;
                     }
@@ -107,33 +255,76 @@ __global__ void cond_entropy(const i64 *xptr, const i32 *xnodes, i64 CX, const i
             }
         }
         __syncwarp();
-        const double Hx = hterm(sx, inv_n) + hterm(n - sx, inv_n);
-        double best = Hx;
+        const i64 sa = a.aptr[k + 1] - a.aptr[k];
+        double bx = __longlong_as_double((long long)a.best[k]);
         for (u32 t = lane; t <= tm; t += 32) {
             const i32 l = keys[t];
-            if (l < 0) continue;
-            best = min(best, cond_candidate(cnts[t], sx, yptr[l + 1] - yptr[l], n, inv_n));
+            if (l >= 0) bx = min(bx, cond_candidate(cnts[t], sa, a.bptr[l + 1] - a.bptr[l], a.n, inv_n));
         }
-        // disjoint partners that can be admitted: |X_k| + |Y_l| > n/2
-        for (i64 b = lane; b < nbig; b += 32) {
-            const i32 l = big[b];
-            const i64 sy = yptr[l + 1] - yptr[l];
-            if (2 * (sx + sy) <= n) continue;
-            u32 h = hash_comm(l) & tm;
-            bool met = false;
-            for (u32 p = 0; p <= tm; ++p) {
-                const i32 x = keys[h];
-                if (x == -1) break;
-                if (x == l) {
-                    met = true;
-                    break;
-                }
-                h = (h + 1u) & tm;
+        for (int o = 16; o; o >>= 1) bx = min(bx, __shfl_xor_sync(FULL_MASK, bx, o));
+        if (lane == 0) a.best[k] = min_bits(bx);
+    }
+}
+
+// Table size of each spilled community: 2 * min(incidences, |B|) rounded up
+// to a power of two.
+__global__ void spill_sizes(const i64 *spill, i64 nk, const i32 *active, const i64 *aptr, const i32 *anodes,
+                            const i32 *bcnt, i64 CB, i64 *tsz) {
+    const int lane = threadIdx.x & 31;
+    const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
+    for (i64 r = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nk; r += warps) {
+        const i32 k = active[spill[r]];
+        i64 s = 0;
+        for (i64 e = aptr[k] + lane; e < aptr[k + 1]; e += 32) s += bcnt[anodes[e]];
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
+        s = min(s, CB);
+        i64 t = 2;
+        while (t < 2 * s) t <<= 1;
+        if (lane == 0) tsz[r] = t;
+    }
+}
+
+// Disjoint pairs that can be admitted (|A| + |B| > n/2): every active A
+// against the listed large communities B; the pair is disjoint unless a merge
+// of the two sorted lists meets a common node.
+__global__ void disjoint_pairs(const i64 *aptr, const i32 *anodes, const i32 *active, i64 n_active,
+                               const i64 *bptr, const i32 *bnodes, const i32 *big, i64 nbig, i64 n,
+                               unsigned long long *best) {
+    const double inv_n = 1.0 / (double)n;
+    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < n_active * nbig; t += (i64)gridDim.x * blockDim.x) {
+        const i32 k = active[t / nbig];
+        const i32 l = big[t % nbig];
+        const i64 sa = aptr[k + 1] - aptr[k], sb = bptr[l + 1] - bptr[l];
+        if (2 * (sa + sb) <= n) continue;
+        const i32 *x = anodes + aptr[k], *y = bnodes + bptr[l];
+        i64 i = 0, j = 0;
+        bool meet = false;
+        while (i < sa && j < sb) {
+            if (x[i] < y[j]) ++i;
+            else if (x[i] > y[j]) ++j;
+            else {
+                meet = true;
+                break;
             }
-            if (!met) best = min(best, cond_candidate(0, sx, sy, n, inv_n));
         }
-        for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(FULL_MASK, best, o));
-        if (lane == 0) term[k] = Hx > 0.0 ? best / Hx : 0.0;
+        if (meet) continue;
+        const double c = cond_candidate(0, sa, sb, n, inv_n);
+        if (c < __builtin_huge_val()) atomicMin(&best[k], min_bits(c));
+    }
+}
+
+// Communities with 2(|B| + 1) > n: the only ones that can satisfy the
+// disjoint admission condition with a community of size >= 1.
+__global__ void list_big(const i64 *ptr, i64 C, i64 n, i32 *big, unsigned long long *nbig) {
+    for (i64 l = (i64)blockIdx.x * blockDim.x + threadIdx.x; l < C; l += (i64)gridDim.x * blockDim.x)
+        if (2 * (ptr[l + 1] - ptr[l] + 1) > n) big[atomicAdd(nbig, 1ull)] = (i32)l;
+}
+
+__global__ void normalise(const i64 *ptr, i64 C, i64 n, const unsigned long long *best, double *term) {
+    const double inv_n = 1.0 / (double)n;
+    for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < C; k += (i64)gridDim.x * blockDim.x) {
+        const double H = entropy(ptr[k + 1] - ptr[k], n, inv_n);
+        term[k] = H > 0.0 ? __longlong_as_double((long long)best[k]) / H : 0.0;
     }
 }
 
@@ -151,88 +342,186 @@ __global__ void sum_fixed(const double *term, i64 m, double *out) {
     if (threadIdx.x == 0) *out = part[0];
 }
 
-__global__ void list_big(const i64 *yptr, i64 CY, i64 n, i32 *big, unsigned long long *nbig) {
-    // communities of Y with 2|Y_l| > n - 2: the only ones that can meet the
-    // disjoint admission condition with some X_k of size >= 1
-    for (i64 l = (i64)blockIdx.x * blockDim.x + threadIdx.x; l < CY; l += (i64)gridDim.x * blockDim.x)
-        if (2 * (yptr[l + 1] - yptr[l] + 1) > n) big[atomicAdd(nbig, 1ull)] = (i32)l;
+template <class T>
+int dev_alloc(T **p, i64 count, cudaStream_t st) {
+    return cuda_status(cudaMallocAsync((void **)p, (size_t)std::max<i64>(count, 1) * sizeof(T), st));
 }
 
-int cond_norm(const ScaleResult &X, const ScaleResult &Y, i64 n, double *out_mean, cudaStream_t st) {
-    const i64 CX = X.n_comms, CY = Y.n_comms;
-    i32 *ycnt = nullptr, *cursor = nullptr, *mlist = nullptr, *tkey = nullptr, *tcnt = nullptr, *big = nullptr;
-    i64 *mptr = nullptr, *tsz = nullptr, *toff = nullptr, *tmp = nullptr;
-    double *term = nullptr, *sum = nullptr;
-    unsigned long long *nbig = nullptr;
+const unsigned GB = 152 * 16;
+
+// node -> communities map of B.
+struct Memberships {
+    i32 *cnt = nullptr, *list = nullptr;
+    i64 *ptr = nullptr;
+};
+
+int build_memberships(const ScaleResult &B, i64 n, Memberships *M, cudaStream_t st) {
+    i32 *cursor = nullptr;
+    i64 *tmp = nullptr;
     int rc = MSCD_OK;
-    const unsigned gb = 152 * 16;
     do {
-        if ((rc = cuda_status(cudaMallocAsync((void **)&ycnt, n * sizeof(i32), st)))) break;
-        if ((rc = cuda_status(cudaMallocAsync((void **)&cursor, n * sizeof(i32), st)))) break;
-        if ((rc = cuda_status(cudaMallocAsync((void **)&mptr, (n + 1) * sizeof(i64), st)))) break;
-        if ((rc = cuda_status(cudaMallocAsync((void **)&tmp, (n + 1) * sizeof(i64), st)))) break;
-        if ((rc = cuda_status(cudaMemsetAsync(ycnt, 0, n * sizeof(i32), st)))) break;
+        if ((rc = dev_alloc(&M->cnt, n, st))) break;
+        if ((rc = dev_alloc(&M->ptr, n + 1, st))) break;
+        if ((rc = dev_alloc(&M->list, B.n_nodes, st))) break;
+        if ((rc = dev_alloc(&cursor, n, st))) break;
+        if ((rc = dev_alloc(&tmp, n + 1, st))) break;
+        if ((rc = cuda_status(cudaMemsetAsync(M->cnt, 0, n * sizeof(i32), st)))) break;
         if ((rc = cuda_status(cudaMemsetAsync(cursor, 0, n * sizeof(i32), st)))) break;
-        count_memberships<<<gb, 256, 0, st>>>(Y.comm_nodes, Y.n_nodes, ycnt);
-        widen_i32<<<gb, 256, 0, st>>>(ycnt, n, tmp);
-        if ((rc = scan_exclusive_i64(tmp, mptr, n, mptr + n, st))) break;
-        if ((rc = cuda_status(cudaMallocAsync((void **)&mlist, std::max<i64>(Y.n_nodes, 1) * sizeof(i32), st)))) break;
-        fill_memberships<<<gb, 256, 0, st>>>(Y.comm_ptr, Y.comm_nodes, CY, mptr, cursor, mlist);
-        if ((rc = cuda_status(cudaMallocAsync((void **)&tsz, (CX + 1) * sizeof(i64), st)))) break;
-        if ((rc = cuda_status(cudaMallocAsync((void **)&toff, (CX + 1) * sizeof(i64), st)))) break;
-        table_sizes<<<gb, 256, 0, st>>>(X.comm_ptr, X.comm_nodes, CX, ycnt, CY, tsz);
-        if ((rc = scan_exclusive_i64(tsz, toff, CX, toff + CX, st))) break;
-        i64 TT = 0;
-        if ((rc = cuda_status(cudaMemcpyAsync(&TT, toff + CX, sizeof(i64), cudaMemcpyDeviceToHost, st)))) break;
-        if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
-        if ((rc = cuda_status(cudaMallocAsync((void **)&tkey, std::max<i64>(TT, 1) * sizeof(i32), st)))) break;
-        if ((rc = cuda_status(cudaMallocAsync((void **)&tcnt, std::max<i64>(TT, 1) * sizeof(i32), st)))) break;
-        if ((rc = cuda_status(cudaMemsetAsync(tkey, 0xff, TT * sizeof(i32), st)))) break;
-        if ((rc = cuda_status(cudaMemsetAsync(tcnt, 0, TT * sizeof(i32), st)))) break;
-        if ((rc = cuda_status(cudaMallocAsync((void **)&big, std::max<i64>(CY, 1) * sizeof(i32), st)))) break;
-        if ((rc = cuda_status(cudaMallocAsync((void **)&nbig, sizeof(unsigned long long), st)))) break;
-        if ((rc = cuda_status(cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), st)))) break;
-        list_big<<<gb, 256, 0, st>>>(Y.comm_ptr, CY, n, big, nbig);
-        unsigned long long h_nbig = 0;
-        if ((rc = cuda_status(cudaMemcpyAsync(&h_nbig, nbig, sizeof(h_nbig), cudaMemcpyDeviceToHost, st)))) break;
-        if ((rc = cuda_status(cudaMallocAsync((void **)&term, std::max<i64>(CX, 1) * sizeof(double), st)))) break;
-        if ((rc = cuda_status(cudaMallocAsync((void **)&sum, sizeof(double), st)))) break;
-        if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
-        cond_entropy<<<gb, 256, 0, st>>>(X.comm_ptr, X.comm_nodes, CX, Y.comm_ptr, CY, mptr, mlist, toff, tkey, tcnt,
-                                         big, (i64)h_nbig, n, term);
-        sum_fixed<<<1, 1024, 0, st>>>(term, CX, sum);
-        double h_sum = 0.0;
-        if ((rc = cuda_status(cudaMemcpyAsync(&h_sum, sum, sizeof(double), cudaMemcpyDeviceToHost, st)))) break;
-        if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
-        *out_mean = h_sum / (double)CX;
+        count_memberships<<<GB, 256, 0, st>>>(B.comm_nodes, B.n_nodes, M->cnt); note_launch();
+        widen_i32<<<GB, 256, 0, st>>>(M->cnt, n, tmp); note_launch();
+        if ((rc = scan_exclusive_i64(tmp, M->ptr, n, M->ptr + n, st))) break;
+        fill_memberships<<<GB, 256, 0, st>>>(B.comm_ptr, B.comm_nodes, B.n_comms, M->ptr, cursor, M->list); note_launch();
     } while (0);
-    cudaFreeAsync(ycnt, st);
     cudaFreeAsync(cursor, st);
-    cudaFreeAsync(mptr, st);
     cudaFreeAsync(tmp, st);
-    cudaFreeAsync(mlist, st);
-    cudaFreeAsync(tsz, st);
-    cudaFreeAsync(toff, st);
-    cudaFreeAsync(tkey, st);
-    cudaFreeAsync(tcnt, st);
+    return rc;
+}
+
+void free_memberships(Memberships *M, cudaStream_t st) {
+    cudaFreeAsync(M->cnt, st);
+    cudaFreeAsync(M->ptr, st);
+    cudaFreeAsync(M->list, st);
+}
+
+// Minimum admitted H(A_k|B) for every active A_k into best[] (one direction).
+int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships &MB, i64 n, const i32 *active,
+                  i64 n_active, unsigned long long *best, cudaStream_t st) {
+    i64 *spill = nullptr, *tsz = nullptr, *toff = nullptr;
+    i32 *tkey = nullptr, *tcnt = nullptr, *big = nullptr;
+    unsigned long long *cnt = nullptr;
+    int rc = MSCD_OK;
+    do {
+        if (n_active == 0) break;
+        if ((rc = dev_alloc(&spill, n_active, st))) break;
+        if ((rc = dev_alloc(&cnt, 2, st))) break;
+        if ((rc = dev_alloc(&big, B.n_comms, st))) break;
+        if ((rc = cuda_status(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st)))) break;
+        DirArgs a{};
+        a.aptr = A.comm_ptr;
+        a.anodes = A.comm_nodes;
+        a.active = active;
+        a.n_active = n_active;
+        a.bptr = B.comm_ptr;
+        a.mptr = MB.ptr;
+        a.mlist = MB.list;
+        a.n = n;
+        a.best = best;
+        a.spill = spill;
+        a.n_spill = cnt;
+        pairs_smem<<<(unsigned)std::min<i64>((n_active + NMI_WARPS - 1) / NMI_WARPS, 152 * 3), NMI_WARPS * 32, 0,
+                     st>>>(a); note_launch();
+        list_big<<<GB, 256, 0, st>>>(B.comm_ptr, B.n_comms, n, big, cnt + 1); note_launch();
+        unsigned long long h[2] = {0, 0};
+        if ((rc = cuda_status(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st)))) break;
+        if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+        const i64 nk = (i64)h[0];
+        if (nk > 0) {
+            if ((rc = dev_alloc(&tsz, nk + 1, st))) break;
+            if ((rc = dev_alloc(&toff, nk + 1, st))) break;
+            spill_sizes<<<GB, 256, 0, st>>>(spill, nk, active, A.comm_ptr, A.comm_nodes, MB.cnt, B.n_comms, tsz); note_launch();
+            if ((rc = scan_exclusive_i64(tsz, toff, nk, toff + nk, st))) break;
+            i64 TT = 0;
+            if ((rc = cuda_status(cudaMemcpyAsync(&TT, toff + nk, sizeof(i64), cudaMemcpyDeviceToHost, st)))) break;
+            if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+            if ((rc = dev_alloc(&tkey, TT, st))) break;
+            if ((rc = dev_alloc(&tcnt, TT, st))) break;
+            if ((rc = cuda_status(cudaMemsetAsync(tkey, 0xff, TT * sizeof(i32), st)))) break;
+            if ((rc = cuda_status(cudaMemsetAsync(tcnt, 0, TT * sizeof(i32), st)))) break;
+            a.toff = toff;
+            a.tkey = tkey;
+            a.tcnt = tcnt;
+            pairs_global<<<GB, 256, 0, st>>>(a, nk); note_launch();
+        }
+        if (h[1] > 0) {
+            disjoint_pairs<<<GB, 256, 0, st>>>(A.comm_ptr, A.comm_nodes, active, n_active, B.comm_ptr, B.comm_nodes,
+                                               big, (i64)h[1], n, best); note_launch();
+        }
+    } while (0);
+    cudaFreeAsync(spill, st);
+    cudaFreeAsync(cnt, st);
     cudaFreeAsync(big, st);
-    cudaFreeAsync(nbig, st);
-    cudaFreeAsync(term, st);
-    cudaFreeAsync(sum, st);
+    if (tsz) cudaFreeAsync(tsz, st);
+    if (toff) cudaFreeAsync(toff, st);
+    if (tkey) cudaFreeAsync(tkey, st);
+    if (tcnt) cudaFreeAsync(tcnt, st);
     return rc;
 }
 
 }  // namespace
 
 int nmi_between(const ScaleResult &X, const ScaleResult &Y, i64 n, double *nmi, cudaStream_t st) {
-    if (X.n_comms <= 0 || Y.n_comms <= 0 || n <= 0) {
+    const i64 CX = X.n_comms, CY = Y.n_comms;
+    if (CX <= 0 || CY <= 0 || n <= 0) {
         *nmi = __builtin_nan("");
         return MSCD_OK;
     }
-    double hxy = 0.0, hyx = 0.0;
-    int rc = cond_norm(X, Y, n, &hxy, st);
-    if (rc == MSCD_OK) rc = cond_norm(Y, X, n, &hyx, st);
-    if (rc != MSCD_OK) return rc;
-    *nmi = 1.0 - 0.5 * (hxy + hyx);
-    return MSCD_OK;
+    u64 *tkey = nullptr;
+    i32 *tval = nullptr, *actX = nullptr, *actY = nullptr;
+    unsigned char *zeroX = nullptr, *zeroY = nullptr;
+    unsigned long long *bestX = nullptr, *bestY = nullptr, *cnt = nullptr;
+    double *termX = nullptr, *termY = nullptr, *sums = nullptr;
+    Memberships MX, MY;
+    int rc = MSCD_OK;
+    i64 T = 2;
+    while (T < 2 * CY) T <<= 1;
+    do {
+        if ((rc = dev_alloc(&tkey, T, st))) break;
+        if ((rc = dev_alloc(&tval, T, st))) break;
+        if ((rc = dev_alloc(&zeroX, CX, st))) break;
+        if ((rc = dev_alloc(&zeroY, CY, st))) break;
+        if ((rc = dev_alloc(&bestX, CX, st))) break;
+        if ((rc = dev_alloc(&bestY, CY, st))) break;
+        if ((rc = dev_alloc(&actX, CX, st))) break;
+        if ((rc = dev_alloc(&actY, CY, st))) break;
+        if ((rc = dev_alloc(&cnt, 2, st))) break;
+        if ((rc = dev_alloc(&termX, CX, st))) break;
+        if ((rc = dev_alloc(&termY, CY, st))) break;
+        if ((rc = dev_alloc(&sums, 2, st))) break;
+        if ((rc = cuda_status(cudaMemsetAsync(tkey, 0, T * sizeof(u64), st)))) break;
+        if ((rc = cuda_status(cudaMemsetAsync(zeroX, 0, CX, st)))) break;
+        if ((rc = cuda_status(cudaMemsetAsync(zeroY, 0, CY, st)))) break;
+        if ((rc = cuda_status(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st)))) break;
+        // identical communities
+        hash_insert<<<GB, 256, 0, st>>>(Y.comm_hash, CY, tkey, tval, T - 1); note_launch();
+        match_identical<<<GB, 256, 0, st>>>(X.comm_ptr, X.comm_nodes, X.comm_hash, CX, Y.comm_ptr, Y.comm_nodes, tkey,
+                                            tval, T - 1, zeroX, zeroY); note_launch();
+        init_best<<<GB, 256, 0, st>>>(X.comm_ptr, CX, n, zeroX, bestX, actX, cnt); note_launch();
+        init_best<<<GB, 256, 0, st>>>(Y.comm_ptr, CY, n, zeroY, bestY, actY, cnt + 1); note_launch();
+        unsigned long long na[2] = {0, 0};
+        if ((rc = cuda_status(cudaMemcpyAsync(na, cnt, sizeof(na), cudaMemcpyDeviceToHost, st)))) break;
+        if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+        // H(X_k|Y) for the X communities without an identical partner
+        if (na[0] > 0) {
+            if ((rc = build_memberships(Y, n, &MY, st))) break;
+            if ((rc = one_direction(X, Y, MY, n, actX, (i64)na[0], bestX, st))) break;
+        }
+        // H(Y_l|X) likewise
+        if (na[1] > 0) {
+            if ((rc = build_memberships(X, n, &MX, st))) break;
+            if ((rc = one_direction(Y, X, MX, n, actY, (i64)na[1], bestY, st))) break;
+        }
+        normalise<<<GB, 256, 0, st>>>(X.comm_ptr, CX, n, bestX, termX); note_launch();
+        normalise<<<GB, 256, 0, st>>>(Y.comm_ptr, CY, n, bestY, termY); note_launch();
+        sum_fixed<<<1, 1024, 0, st>>>(termX, CX, sums); note_launch();
+        sum_fixed<<<1, 1024, 0, st>>>(termY, CY, sums + 1); note_launch();
+        double hs[2] = {0.0, 0.0};
+        if ((rc = cuda_status(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st)))) break;
+        if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+        *nmi = 1.0 - 0.5 * (hs[0] / (double)CX + hs[1] / (double)CY);
+    } while (0);
+    free_memberships(&MX, st);
+    free_memberships(&MY, st);
+    cudaFreeAsync(tkey, st);
+    cudaFreeAsync(tval, st);
+    cudaFreeAsync(zeroX, st);
+    cudaFreeAsync(zeroY, st);
+    cudaFreeAsync(bestX, st);
+    cudaFreeAsync(bestY, st);
+    cudaFreeAsync(actX, st);
+    cudaFreeAsync(actY, st);
+    cudaFreeAsync(cnt, st);
+    cudaFreeAsync(termX, st);
+    cudaFreeAsync(termY, st);
+    cudaFreeAsync(sums, st);
+    return rc != MSCD_OK ? rc : cuda_status(cudaGetLastError());
 }

@@ -62,11 +62,11 @@ int scan_exclusive_i64(const i64 *in, i64 *out, i64 n, i64 *total_dev, cudaStrea
     const i64 nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     i64 *sums = nullptr;
     MSCD_CUDA(cudaMallocAsync((void **)&sums, (size_t)nb * sizeof(i64), st));
-    scan_tiles<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, sums);
+    scan_tiles<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, sums); note_launch();
     int rc = MSCD_OK;
     if (nb > 1) {
         rc = scan_exclusive_i64(sums, sums, nb, total_dev, st);
-        if (rc == MSCD_OK) add_tile_offsets<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(out, n, sums);
+        if (rc == MSCD_OK) { add_tile_offsets<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(out, n, sums); note_launch(); }
     } else if (total_dev) {
         cudaMemcpyAsync(total_dev, sums, sizeof(i64), cudaMemcpyDeviceToDevice, st);
     }

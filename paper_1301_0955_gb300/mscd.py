@@ -31,23 +31,31 @@ vp = C.c_void_p
 
 class mscd_params(C.Structure):
     _fields_ = [("struct_size", C.c_int32), ("warps_per_block", C.c_int32), ("smem_slots", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("max_rounds", C.c_int64)]
+                ("blocks_per_sm", C.c_int32), ("mid_slots", C.c_int32), ("global_warps_per_sm", C.c_int32),
+                ("max_rounds", C.c_int64)]
 
 
 class mscd_run_stats(C.Structure):
     _fields_ = [("units", C.c_int64), ("edges_scanned", C.c_int64), ("adds", C.c_int64), ("removes", C.c_int64),
                 ("slow_decisions", C.c_int64), ("undecided", C.c_int64), ("overflow_units", C.c_int64),
                 ("grow_launches", C.c_int64), ("member_entries", C.c_int64), ("ms_grow", C.c_double),
-                ("ms_dedup", C.c_double), ("ms_stability", C.c_double), ("ms_total", C.c_double)]
+                ("ms_dedup", C.c_double), ("ms_stability", C.c_double), ("ms_total", C.c_double),
+                ("launch_cap", C.c_int32 * 8), ("launch_smem", C.c_int32 * 8), ("launch_units", C.c_int64 * 8),
+                ("launch_ms", C.c_double * 8)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("launch_")}
+        n = min(8, self.grow_launches)
+        d["launches"] = [dict(cap=self.launch_cap[i], smem=self.launch_smem[i], units=self.launch_units[i],
+                              ms=self.launch_ms[i]) for i in range(n)]
+        return d
 
 
 # name -> (restype, argtypes)
 SIGNATURES = {
     "mscd_strerror": (C.c_char_p, [C.c_int]),
     "mscd_version": (C.c_int, []),
+    "mscd_launch_count": (C.c_int64, []),
     "mscd_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(mscd_params)]),
     "mscd_destroy": (C.c_int, [vp]),
     "mscd_graph_load_csr": (C.c_int, [vp, C.c_int64, vp, vp, vp, C.c_uint32, i32p]),
@@ -118,10 +126,11 @@ def scales_logspaced(vmin: float, a: float, x: int) -> np.ndarray:
 class Context:
     """One mscd context on one device."""
 
-    def __init__(self, device: int = 0, warps_per_block: int = 0, smem_slots: int = 0, blocks_per_sm: int = 0,
-                 max_rounds: int = 0):
+    def __init__(self, device: int = 0, smem_slots: int = 0, blocks_per_sm: int = 0, max_rounds: int = 0,
+                 warps_per_block: int = 0, mid_slots: int = 0, global_warps_per_sm: int = 0):
         L = load()
-        p = mscd_params(C.sizeof(mscd_params), warps_per_block, smem_slots, blocks_per_sm, max_rounds)
+        p = mscd_params(C.sizeof(mscd_params), warps_per_block, smem_slots, blocks_per_sm, mid_slots,
+                        global_warps_per_sm, max_rounds)
         h = vp()
         _check(L.mscd_create(C.byref(h), device, C.byref(p)), "mscd_create")
         self.h = h

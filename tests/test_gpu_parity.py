@@ -167,19 +167,31 @@ def test_planted_full_parity(orc, ctx):
     ctx.free_graph(gid)
 
 
-def test_slot_class_escalation(orc, ctx):
-    """A tiny shared-memory class forces most units into larger global-memory
-    classes; results must not change."""
+@pytest.mark.parametrize("weighted", [False, True])
+def test_slot_class_escalation(orc, ctx, weighted):
+    """Tiny shared-memory classes force units through every class: two
+    shared-memory classes, then global arenas of growing capacity.  Results
+    must not change."""
     from paper_1301_0955_gb300 import mscd
 
-    c2 = mscd.Context(0, smem_slots=32, warps_per_block=4)
+    c2 = mscd.Context(0, smem_slots=32, mid_slots=64)
     g = synth.config_graph(0)
+    w = None
+    if weighted:
+        w = np.random.default_rng(4).uniform(0.5, 2.0, g.nnz // 2).astype(np.float32)
+        iu = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+        up = iu < g.col
+        rp, col, w = synth.to_csr(g.n, iu[up], g.col[up], w[: int(up.sum())])
+        g = synth.CSRGraph(g.n, rp, col, w, g.labels, g.name)
     G = oracle_graph(orc, g)
     alphas = np.array([1.0, 0.6, 0.5])
     seeds = np.arange(0, g.n, 3, dtype=np.int32)
-    gid = c2.load_csr(g.n, g.row_ptr, g.col)
+    gid = c2.load_csr(g.n, g.row_ptr, g.col, g.w)
     assert c2.run(gid, alphas, seeds) == 0
-    assert c2.run_stats()["overflow_units"] > 0
+    st = c2.run_stats()
+    assert st["overflow_units"] > 0
+    classes = {(l["cap"], l["smem"]) for l in st["launches"]}
+    assert (32, 1) in classes and (64, 1) in classes and any(cap > 64 and not sm for cap, sm in classes)
     compare_units(orc, c2, G, alphas, seeds)
     c2.close()
 
