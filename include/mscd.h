@@ -197,6 +197,37 @@ int mscd_get_stability(mscd_ctx *ctx, double *nmi_succ, double *nmi_win3, double
 /* Totals of the last run. */
 int mscd_get_run_stats(mscd_ctx *ctx, mscd_run_stats *out);
 
+/* Growth of every (scale, seed) unit without allocating device memory during
+ * the call.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc while they run (a process with a fixed
+ * device-memory plan, an allocator that must not be bypassed, a latency
+ * path that cannot take an allocation's synchronisation).  It grows the same
+ * communities as mscd_run (no dedup, no stability) and allocates nothing:
+ * the growth scratch lives in one 64 MiB device array built into the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   graph_id   a graph resident in ctx (loaded earlier by mscd_graph_load_csr)
+ *   alphas     host double[n_scales], finite and > 0, n_scales <= 256
+ *   seeds      device int32[n_seeds] node ids, or NULL for every node
+ *   outputs    device buffers owned by the caller, unit u = scale*n_seeds+seed:
+ *              out_nodes int32[out_cap] (member lists, each ascending, at
+ *              out_offset[u], length out_len[u]), out_fitness double[U],
+ *              out_stats int64[U*MSCD_NSTATS], out_status int32[U],
+ *              out_hash uint64[U] (hash of each member list)
+ *   *n_nodes_needed  total member-list length of all units (host)
+ *   cuda_stream      stream to order the work on (NULL = default stream)
+ * Limits and errors: at most 2^20 units per call and 8192 touched nodes per
+ * unit (MSCD_ERANGE when a unit needs more); MSCD_ESMALL when out_cap <
+ * *n_nodes_needed; MSCD_EINVAL for bad arguments or seeds.  The first call
+ * on a device looks up the array's device address once (make that first call
+ * before any stream capture).  Every call reuses the same array, which keeps
+ * the previous call's contents (the call clears what must start at zero):
+ * calls that overlap on the GPU, on any stream or context of one device,
+ * race on it and must not be issued. */
+int mscd_grow_noalloc(mscd_ctx *ctx, int32_t graph_id, const double *alphas, int32_t n_scales,
+                      const int32_t *seeds, int64_t n_seeds, int32_t *out_nodes, int64_t out_cap,
+                      int64_t *out_offset, int32_t *out_len, double *out_fitness, int64_t *out_stats,
+                      int32_t *out_status, uint64_t *out_hash, int64_t *n_nodes_needed, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -207,6 +207,14 @@ struct Task {
 
 }  // namespace
 
+bool ctx_graph(mscd_ctx *c, int32_t graph_id, DevGraph *g, int *device) {
+    GraphRec *r = find_graph(c, graph_id);
+    if (!r) return false;
+    *g = r->g;
+    *device = c->device;
+    return true;
+}
+
 extern "C" {
 
 const char *mscd_strerror(int s) {

@@ -45,6 +45,10 @@ void note_launch();
 // through *total_dev (device pointer, may be null).  Work buffer handled inside.
 int scan_exclusive_i64(const i64 *in, i64 *out, i64 n, i64 *total_dev, cudaStream_t st);
 
+// A context's resident graph and device (false for an unknown id).
+struct mscd_ctx;
+bool ctx_graph(mscd_ctx *c, int32_t graph_id, DevGraph *g, int *device);
+
 // Graph preparation (checks, exact weights, degrees, log degrees).
 int graph_prepare(i64 n, const i64 *rp_dev, const i32 *col_dev, const float *w_dev, DevGraph *g, i64 **wfx_out,
                   i64 **k_out, float **logk_out, cudaStream_t st);

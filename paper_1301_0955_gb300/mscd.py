@@ -69,6 +69,8 @@ SIGNATURES = {
     "mscd_get_communities": (C.c_int, [vp, C.c_int32, i64p, C.c_int64, i32p, C.c_int64, f64p, i32p, i64p, i64p]),
     "mscd_get_stability": (C.c_int, [vp, f64p, f64p, f64p]),
     "mscd_get_run_stats": (C.c_int, [vp, C.POINTER(mscd_run_stats)]),
+    "mscd_grow_noalloc": (C.c_int, [vp, C.c_int32, f64p, C.c_int32, vp, C.c_int64, vp, C.c_int64, vp, vp, vp, vp,
+                                    vp, vp, i64p, vp]),
 }
 
 _lib = None
@@ -255,6 +257,24 @@ class Context:
         _check(load().mscd_get_stability(self.h, a.ctypes.data_as(f64p), b.ctypes.data_as(f64p),
                                          c.ctypes.data_as(f64p)), "mscd_get_stability")
         return a[: S - 1], b, c
+
+    def grow_noalloc(self, gid: int, alphas, seeds, out: dict, stream=None):
+        """Growth without device allocation (see mscd_grow_noalloc).  ``seeds`` is
+        a CUDA int32 tensor or None; ``out`` holds CUDA tensors: nodes (int32),
+        offset (int64), len (int32), fitness (float64), stats (int64, U x 8),
+        status (int32), hash (int64).  Returns (status, n_nodes_needed)."""
+        alphas = np.ascontiguousarray(alphas, np.float64)
+        sp = None if seeds is None else seeds.data_ptr()
+        n_seeds = 0 if seeds is None else int(seeds.shape[0])
+        need = C.c_int64()
+        st = None
+        if stream is not None:
+            st = stream if isinstance(stream, int) else stream.cuda_stream
+        rc = load().mscd_grow_noalloc(self.h, gid, alphas.ctypes.data_as(f64p), len(alphas), sp, n_seeds,
+                                      out["nodes"].data_ptr(), int(out["nodes"].numel()), out["offset"].data_ptr(),
+                                      out["len"].data_ptr(), out["fitness"].data_ptr(), out["stats"].data_ptr(),
+                                      out["status"].data_ptr(), out["hash"].data_ptr(), C.byref(need), st)
+        return rc, need.value
 
     def run_stats(self) -> dict:
         s = mscd_run_stats()
