@@ -78,7 +78,7 @@ typedef struct mscd_ctx mscd_ctx;
 /* Tuning and limits.  Zero fields take the defaults. */
 typedef struct mscd_params {
     int32_t struct_size;     /* sizeof(mscd_params)                                     */
-    int32_t warps_per_block; /* global-arena classes: warps (units) per CTA (8)          */
+    int32_t warps_per_block; /* reserved (0)                                             */
     int32_t smem_slots;      /* node slots of the first shared-memory class (power of 2
                                 >= 32; 0 = 1024, or 512 when weighted slots do not fit) */
     int32_t blocks_per_sm;   /* first class: CTAs per SM (0 = from occupancy)           */

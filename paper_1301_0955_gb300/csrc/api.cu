@@ -527,7 +527,7 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
                 blocks = per_sm * c->sm_count;
             } else {
                 a.use_smem = 0;
-                const int wpc = c->p.warps_per_block;
+                const int wpc = GLOBAL_CTA_THREADS / 32;
                 const size_t budget = (size_t)4 << 30;
                 i64 warps = std::max<i64>(
                     1, std::min<i64>((i64)(budget / a.state_bytes), (i64)c->sm_count * c->p.global_warps_per_sm));

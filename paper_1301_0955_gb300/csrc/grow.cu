@@ -69,6 +69,7 @@ struct State {
     float *key;           // [C] ranking key while queued, else -inf
     i32 *id;              // [C] node id
     int *gmax;            // [C/32] upper bound of the group's largest key (ord image)
+    int *qmax;            // [C/32] upper bound of the group's largest d_in / k (ord image)
     HT *hsh;              // [2C] bucket -> slot + 1 (0 = empty)
     unsigned char *flag;  // [C]
     int C, H;
@@ -79,7 +80,7 @@ struct State {
 template <class VT, class HT, bool WEIGHTED>
 __host__ __device__ __forceinline__ size_t state_bytes_t(int C) {
     const size_t per = 2 * sizeof(VT) + 4 + 4 + 2 * sizeof(HT) + 1;
-    const size_t b = (size_t)C * per + 4 * (size_t)(C / 32);
+    const size_t b = (size_t)C * per + 8 * (size_t)(C / 32);
     return (b + 127) & ~(size_t)127;
 }
 
@@ -98,6 +99,8 @@ __device__ __forceinline__ State<VT, HT, WEIGHTED> carve(unsigned char *base, in
     s.id = (i32 *)(base + o);
     o += 4 * (size_t)C;
     s.gmax = (int *)(base + o);
+    o += 4 * (size_t)(C / 32);
+    s.qmax = (int *)(base + o);
     o += 4 * (size_t)(C / 32);
     s.hsh = (HT *)(base + o);
     o += 2 * sizeof(HT) * (size_t)C;
@@ -127,7 +130,7 @@ struct Unit {
     int ns;  // slots in use
     i32 seed;
     double alpha;
-    float alpha32, E2;
+    float alpha32, E2, kmaxf;
     i64 edges, adds, removes, rounds;
     u32 xflags;  // EXACT_* of this lane's decisions
     bool ovf;    // slot capacity exceeded
@@ -282,10 +285,19 @@ __device__ void rebuild_groups(const S &st, const Unit &U) {
     const int G = (U.ns + 31) >> 5;
     for (int g = 0; g < G; ++g) {
         const int i = g * 32 + lane;
-        const int o = __reduce_max_sync(FULL_MASK, i < U.ns ? ord(st.key[i]) : ORD_NEG_INF);
-        if (lane == 0) st.gmax[g] = o;
+        const float k = i < U.ns ? st.key[i] : NEG_INF;
+        const int o = __reduce_max_sync(FULL_MASK, ord(k));
+        const int q = __reduce_max_sync(
+            FULL_MASK, k == NEG_INF ? ORD_NEG_INF : ord((float)(i64)st.din[i] / (float)(i64)st.kdeg[i]));
+        if (lane == 0) {
+            st.gmax[g] = o;
+            st.qmax[g] = q;
+        }
     }
-    for (int g = G + lane; g < st.C / 32; g += 32) st.gmax[g] = ORD_NEG_INF;
+    for (int g = G + lane; g < st.C / 32; g += 32) {
+        st.gmax[g] = ORD_NEG_INF;
+        st.qmax[g] = ORD_NEG_INF;
+    }
     __syncwarp();
 }
 
@@ -327,28 +339,33 @@ __device__ int queue_top(const S &st, Unit &U) {
 }
 
 // Highest-ranked queued slot that passes the add test at the current K, V.
+// A node passes only if 2 d (V + k) > alpha K k (the filter below), so only if
+// d / k > alpha K / (2 (V + k_max)): groups whose d/k bound is below that are
+// skipped.  (The threshold and the d/k values carry a few roundings of 2^-24
+// each; the 2^-16 margin keeps the skip one-sided.)
 template <class S>
 __device__ int best_passing(const S &st, Unit &U) {
     const int lane = threadIdx.x & 31;
+    const int G = (U.ns + 31) >> 5;
+    const float tau = U.alpha32 * (float)U.K / (2.0f * ((float)U.V + U.kmaxf)) * (1.0f - 0x1p-16f);
+    const int otau = ord(tau);
     int best = -1;
     float bk = NEG_INF;
-    for (int b = 0; b < U.ns; b += 32 * UNROLL) {
-        float kv[UNROLL];
-#pragma unroll
-        for (int j = 0; j < UNROLL; ++j) {
-            const int i = b + 32 * j + lane;
-            kv[j] = i < U.ns ? st.key[i] : NEG_INF;
-        }
-#pragma unroll
-        for (int j = 0; j < UNROLL; ++j) {
-            if (kv[j] == NEG_INF) continue;
-            const int i = b + 32 * j + lane;
+    for (int base = 0; base < G; base += 32) {
+        const int g = base + lane;
+        u32 ball = __ballot_sync(FULL_MASK, g < G && st.qmax[g] >= otau);
+        while (ball) {
+            const int gg = base + __ffs(ball) - 1;
+            ball &= ball - 1;
+            const int i = gg * 32 + lane;
+            const float k = i < U.ns ? st.key[i] : NEG_INF;
+            if (k == NEG_INF) continue;
             const i64 d = st.din[i], kd = st.kdeg[i];
             if (!exact::add_possible(U.K, U.V, d, kd, U.alpha32)) continue;
             if (!exact::add_test(U.K, U.V, d, kd, U.alpha, U.alpha32, &U.xflags)) continue;
-            if (best < 0 || ranks_before(st, i, kv[j], best, bk, U)) {
+            if (best < 0 || ranks_before(st, i, k, best, bk, U)) {
                 best = i;
-                bk = kv[j];
+                bk = k;
             }
         }
     }
@@ -356,24 +373,24 @@ __device__ int best_passing(const S &st, Unit &U) {
     return best;
 }
 
-// Pop (reject) every queued slot ranked before `best` (all of them if best
-// < 0), then recompute every group best.
+// Pop (reject) every queued slot ranked before `best`.  Such a slot has a key
+// above key(best) - E2, so only groups whose bound reaches key(best) - 2 E2
+// are visited.  Group bounds stay upper bounds.
 template <class S>
 __device__ void drop_before(const S &st, int best, Unit &U) {
     const int lane = threadIdx.x & 31;
-    const float bk = best >= 0 ? st.key[best] : 0.0f;
-    for (int b = 0; b < U.ns; b += 32 * UNROLL) {
-        float kv[UNROLL];
-#pragma unroll
-        for (int j = 0; j < UNROLL; ++j) {
-            const int i = b + 32 * j + lane;
-            kv[j] = i < U.ns ? st.key[i] : NEG_INF;
-        }
-#pragma unroll
-        for (int j = 0; j < UNROLL; ++j) {
-            if (kv[j] == NEG_INF) continue;
-            const int i = b + 32 * j + lane;
-            if (best < 0 || ranks_before(st, i, kv[j], best, bk, U)) st.key[i] = NEG_INF;
+    const int G = (U.ns + 31) >> 5;
+    const float bk = st.key[best];
+    const int othr = ord(bk - 2.0f * U.E2);
+    for (int base = 0; base < G; base += 32) {
+        const int g = base + lane;
+        u32 ball = __ballot_sync(FULL_MASK, g < G && st.gmax[g] >= othr);
+        while (ball) {
+            const int gg = base + __ffs(ball) - 1;
+            ball &= ball - 1;
+            const int i = gg * 32 + lane;
+            const float k = i < U.ns ? st.key[i] : NEG_INF;
+            if (k != NEG_INF && ranks_before(st, i, k, best, bk, U)) st.key[i] = NEG_INF;
         }
     }
     __syncwarp();
@@ -411,7 +428,10 @@ __device__ void expand(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Uni
                 upd = true;
             }
         }
-        if (upd) atomicMax(&st.gmax[s >> 5], ord(k));
+        if (upd) {
+            atomicMax(&st.gmax[s >> 5], ord(k));
+            atomicMax(&st.qmax[s >> 5], ord((float)(i64)st.din[s] / (float)(i64)st.kdeg[s]));
+        }
     }
     __syncwarp();
     U.edges += re - rs;
@@ -578,6 +598,7 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
     U.alpha32 = (float)U.alpha;
     U.seed = a.seeds ? a.seeds[si] : (i32)si;
     U.E2 = 2.0f * 0x1p-20f * (1.0f + U.alpha32) * (1.0f + a.log_kmax);
+    U.kmaxf = (float)G.kmax;
     U.K = 0;
     U.V = G.k[U.seed];
     U.ns = 0;
@@ -612,8 +633,10 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
             int s = top;
             if (!exact::add_test(U.K, U.V, (i64)st.din[top], (i64)st.kdeg[top], U.alpha, U.alpha32, &U.xflags)) {
                 s = best_passing(st, U);
-                drop_before(st, s, U);
+                // none passes: every queued node is popped and rejected, the grow
+                // pass ends (the next round rebuilds every key)
                 if (s < 0) break;
+                drop_before(st, s, U);
             }
             accept(st, a, U, s);
             added++;
@@ -651,8 +674,8 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
 // One unit per warp, persistent: units are taken from a global counter until
 // the work list is exhausted.  State: dynamic shared memory (warp w of the
 // CTA at w * state_bytes) or the global arena (warp at its global index).
-template <class VT, class HT, bool WEIGHTED>
-__global__ void __launch_bounds__(GROW_MAX_THREADS) grow_kernel(GrowArgs a) {
+template <class VT, class HT, bool WEIGHTED, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) grow_kernel(GrowArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const i64 gw = (i64)blockIdx.x * (blockDim.x >> 5) + wib;
@@ -670,19 +693,29 @@ __global__ void __launch_bounds__(GROW_MAX_THREADS) grow_kernel(GrowArgs a) {
     }
 }
 
-template <class VT, class HT, bool WEIGHTED>
-int launch_t(const GrowArgs &a, int blocks, int threads, size_t smem, cudaStream_t st, int *occ) {
+template <class VT, class HT, bool WEIGHTED, int MAXT, int MINB>
+int launch_k(const GrowArgs &a, int blocks, int threads, size_t smem, cudaStream_t st, int *occ) {
+    auto k = grow_kernel<VT, HT, WEIGHTED, MAXT, MINB>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(grow_kernel<VT, HT, WEIGHTED>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_status(e);
     }
-    if (occ)
-        return cuda_status(
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, grow_kernel<VT, HT, WEIGHTED>, threads, smem));
-    grow_kernel<VT, HT, WEIGHTED><<<blocks, threads, smem, st>>>(a);
+    if (occ) return cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, threads, smem));
+    k<<<blocks, threads, smem, st>>>(a);
     note_launch();
     return cuda_status(cudaGetLastError());
+}
+
+// Shared-memory classes: CTAs of up to 16 one-warp units (shared memory
+// bounds the count).  Global-arena classes: CTAs of GLOBAL_CTA_THREADS with
+// registers capped so that GLOBAL_MIN_BLOCKS of them fit an SM.
+#ifndef GLOBAL_MIN_BLOCKS
+#define GLOBAL_MIN_BLOCKS 2
+#endif
+template <class VT, class HT, bool WEIGHTED>
+int launch_t(const GrowArgs &a, int blocks, int threads, size_t smem, cudaStream_t st, int *occ) {
+    if (a.use_smem) return launch_k<VT, HT, WEIGHTED, GROW_MAX_THREADS, 1>(a, blocks, threads, smem, st, occ);
+    return launch_k<VT, HT, WEIGHTED, GLOBAL_CTA_THREADS, GLOBAL_MIN_BLOCKS>(a, blocks, threads, smem, st, occ);
 }
 
 typedef unsigned short u16;

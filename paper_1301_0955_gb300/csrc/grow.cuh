@@ -4,6 +4,7 @@
 #include "common.cuh"
 
 #define GROW_MAX_THREADS 512
+#define GLOBAL_CTA_THREADS 256  // threads per CTA of the global-arena classes
 
 struct GrowArgs {
     DevGraph G;

@@ -24,8 +24,9 @@
 // The intersections of the sharing pairs are counted by a warp per community:
 // it walks its members' lists of partner communities (the lanes spread over
 // one list at a time, whose entries are distinct) and counts in a
-// shared-memory hash; a community that meets too many partners is redone
-// with a global-memory table of its own.  Minima are kept as the bits of
+// shared-memory hash; a community that meets too many partners is redone by
+// a whole CTA with a larger shared-memory table, and beyond that with a
+// global-memory table of its own.  Minima are kept as the bits of
 // non-negative doubles; per-community terms are summed in a fixed order, so
 // the value is deterministic.
 #include <algorithm>
@@ -225,13 +226,14 @@ __global__ void __launch_bounds__(NMI_WARPS * 32) pairs_smem(DirArgs a) {
     }
 }
 
-// Warp per spilled community: the same with a global table of its own.
-__global__ void pairs_global(DirArgs a, i64 nk) {
+// Warp per listed community (positions in `active`): the same with a global
+// table of its own.
+__global__ void pairs_global(DirArgs a, const i64 *list, i64 nk) {
     const int lane = threadIdx.x & 31;
     const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
     const double inv_n = 1.0 / (double)a.n;
     for (i64 r = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nk; r += warps) {
-        const i32 k = a.active[a.spill[r]];
+        const i32 k = a.active[list[r]];
         i32 *keys = a.tkey + a.toff[r];
         i32 *cnts = a.tcnt + a.toff[r];
         const u32 tm = (u32)(a.toff[r + 1] - a.toff[r] - 1);
@@ -266,14 +268,87 @@ __global__ void pairs_global(DirArgs a, i64 nk) {
     }
 }
 
+constexpr int BLK_WARPS = 16;
+constexpr int BLK_TABLE = 16384;  // shared-memory hash entries of one CTA
+
+// CTA per community spilled by pairs_smem: its members are spread over the
+// warps, a 16384-entry shared-memory table counts the intersections; a
+// community meeting more than half of that is listed for pairs_global.
+__global__ void __launch_bounds__(BLK_WARPS * 32) pairs_block(DirArgs a, const i64 *list, i64 nk, i64 *spill2,
+                                                              unsigned long long *n_spill2) {
+    extern __shared__ i32 tab[];
+    i32 *keys = tab, *cnts = tab + BLK_TABLE;
+    __shared__ int fill, over;
+    __shared__ double wmin[BLK_WARPS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const double inv_n = 1.0 / (double)a.n;
+    for (i64 r = blockIdx.x; r < nk; r += gridDim.x) {
+        const i64 q = list[r];
+        const i32 k = a.active[q];
+        for (int t = threadIdx.x; t < BLK_TABLE; t += BLK_WARPS * 32) {
+            keys[t] = -1;
+            cnts[t] = 0;
+        }
+        if (threadIdx.x == 0) {
+            fill = 0;
+            over = 0;
+        }
+        __syncthreads();
+        for (i64 e = a.aptr[k] + w; e < a.aptr[k + 1]; e += BLK_WARPS) {
+            if (*(volatile int *)&over) break;
+            const i32 u = a.anodes[e];
+            for (i64 j = a.mptr[u] + lane; j < a.mptr[u + 1]; j += 32) {
+                const i32 l = a.mlist[j];
+                u32 h = hash_comm(l) & (BLK_TABLE - 1);
+                for (int p = 0; p < BLK_TABLE; ++p) {
+                    i32 cur = keys[h];
+                    if (cur == -1) {
+                        cur = atomicCAS(&keys[h], -1, l);
+                        if (cur == -1) {
+                            if (atomicAdd(&fill, 1) >= BLK_TABLE / 2) over = 1;
+                            cur = l;
+                        }
+                    }
+                    if (cur == l) {
+                        atomicAdd(&cnts[h], 1);
+                        break;
+                    }
+                    h = (h + 1u) & (BLK_TABLE - 1);
+                }
+            }
+        }
+        __syncthreads();
+        if (over) {
+            if (threadIdx.x == 0) spill2[atomicAdd(n_spill2, 1ull)] = q;
+            __syncthreads();
+            continue;
+        }
+        const i64 sa = a.aptr[k + 1] - a.aptr[k];
+        double bx = __builtin_huge_val();
+        for (int t = threadIdx.x; t < BLK_TABLE; t += BLK_WARPS * 32) {
+            const i32 l = keys[t];
+            if (l >= 0) bx = min(bx, cond_candidate(cnts[t], sa, a.bptr[l + 1] - a.bptr[l], a.n, inv_n));
+        }
+        for (int o = 16; o; o >>= 1) bx = min(bx, __shfl_xor_sync(FULL_MASK, bx, o));
+        if (lane == 0) wmin[w] = bx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = __longlong_as_double((long long)a.best[k]);
+            for (int i = 0; i < BLK_WARPS; ++i) m = min(m, wmin[i]);
+            a.best[k] = min_bits(m);
+        }
+        __syncthreads();
+    }
+}
+
 // Table size of each spilled community: 2 * min(incidences, |B|) rounded up
 // to a power of two.
-__global__ void spill_sizes(const i64 *spill, i64 nk, const i32 *active, const i64 *aptr, const i32 *anodes,
+__global__ void spill_sizes(const i64 *list, i64 nk, const i32 *active, const i64 *aptr, const i32 *anodes,
                             const i32 *bcnt, i64 CB, i64 *tsz) {
     const int lane = threadIdx.x & 31;
     const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
     for (i64 r = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nk; r += warps) {
-        const i32 k = active[spill[r]];
+        const i32 k = active[list[r]];
         i64 s = 0;
         for (i64 e = aptr[k] + lane; e < aptr[k + 1]; e += 32) s += bcnt[anodes[e]];
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
@@ -386,16 +461,16 @@ void free_memberships(Memberships *M, cudaStream_t st) {
 // Minimum admitted H(A_k|B) for every active A_k into best[] (one direction).
 int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships &MB, i64 n, const i32 *active,
                   i64 n_active, unsigned long long *best, cudaStream_t st) {
-    i64 *spill = nullptr, *tsz = nullptr, *toff = nullptr;
+    i64 *spill = nullptr, *spill2 = nullptr, *tsz = nullptr, *toff = nullptr;
     i32 *tkey = nullptr, *tcnt = nullptr, *big = nullptr;
     unsigned long long *cnt = nullptr;
     int rc = MSCD_OK;
     do {
         if (n_active == 0) break;
         if ((rc = dev_alloc(&spill, n_active, st))) break;
-        if ((rc = dev_alloc(&cnt, 2, st))) break;
+        if ((rc = dev_alloc(&cnt, 3, st))) break;
         if ((rc = dev_alloc(&big, B.n_comms, st))) break;
-        if ((rc = cuda_status(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st)))) break;
+        if ((rc = cuda_status(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), st)))) break;
         DirArgs a{};
         a.aptr = A.comm_ptr;
         a.anodes = A.comm_nodes;
@@ -414,11 +489,26 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
         unsigned long long h[2] = {0, 0};
         if ((rc = cuda_status(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st)))) break;
         if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
-        const i64 nk = (i64)h[0];
+        i64 nk = (i64)h[0];
+        const i64 *list = spill;
+        if (nk > 0) {
+            // middle tier: one community per CTA with a large shared-memory table
+            if ((rc = dev_alloc(&spill2, nk, st))) break;
+            const size_t bsm = 2 * sizeof(i32) * BLK_TABLE;
+            if ((rc = cuda_status(cudaFuncSetAttribute(pairs_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)bsm))))
+                break;
+            pairs_block<<<(unsigned)std::min<i64>(nk, 152), BLK_WARPS * 32, bsm, st>>>(a, spill, nk, spill2, cnt + 2); note_launch();
+            unsigned long long h2 = 0;
+            if ((rc = cuda_status(cudaMemcpyAsync(&h2, cnt + 2, sizeof(h2), cudaMemcpyDeviceToHost, st)))) break;
+            if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+            nk = (i64)h2;
+            list = spill2;
+        }
         if (nk > 0) {
             if ((rc = dev_alloc(&tsz, nk + 1, st))) break;
             if ((rc = dev_alloc(&toff, nk + 1, st))) break;
-            spill_sizes<<<GB, 256, 0, st>>>(spill, nk, active, A.comm_ptr, A.comm_nodes, MB.cnt, B.n_comms, tsz); note_launch();
+            spill_sizes<<<GB, 256, 0, st>>>(list, nk, active, A.comm_ptr, A.comm_nodes, MB.cnt, B.n_comms, tsz); note_launch();
             if ((rc = scan_exclusive_i64(tsz, toff, nk, toff + nk, st))) break;
             i64 TT = 0;
             if ((rc = cuda_status(cudaMemcpyAsync(&TT, toff + nk, sizeof(i64), cudaMemcpyDeviceToHost, st)))) break;
@@ -430,7 +520,7 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
             a.toff = toff;
             a.tkey = tkey;
             a.tcnt = tcnt;
-            pairs_global<<<GB, 256, 0, st>>>(a, nk); note_launch();
+            pairs_global<<<GB, 256, 0, st>>>(a, list, nk); note_launch();
         }
         if (h[1] > 0) {
             disjoint_pairs<<<GB, 256, 0, st>>>(A.comm_ptr, A.comm_nodes, active, n_active, B.comm_ptr, B.comm_nodes,
@@ -438,6 +528,7 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
         }
     } while (0);
     cudaFreeAsync(spill, st);
+    if (spill2) cudaFreeAsync(spill2, st);
     cudaFreeAsync(cnt, st);
     cudaFreeAsync(big, st);
     if (tsz) cudaFreeAsync(tsz, st);
