@@ -85,6 +85,8 @@ typedef struct mscd_params {
     int32_t mid_slots;       /* node slots of an optional second shared-memory class
                                 (power of 2 >= 32; 0 = none)                            */
     int32_t global_warps_per_sm; /* global-arena classes: resident units per SM (16)     */
+    int32_t global_slots;    /* node slots of the first global-arena class (power of 2;
+                                0 = 8 times the last shared-memory class)                */
     int64_t max_rounds;      /* grow/prune repetitions per unit before ETIMEOUT (1e6)     */
 } mscd_params;
 

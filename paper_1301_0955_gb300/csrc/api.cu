@@ -258,6 +258,10 @@ int mscd_create(mscd_ctx **out, int device, const mscd_params *params) {
     if (c->p.smem_slots < 0) c->p.smem_slots = 0;
     if (c->p.mid_slots < 0) c->p.mid_slots = 0;
     if (c->p.global_warps_per_sm <= 0) c->p.global_warps_per_sm = 16;
+    if (c->p.global_slots < 0 || (c->p.global_slots & (c->p.global_slots - 1))) {
+        delete c;
+        return MSCD_EINVAL;
+    }
     if (c->p.warps_per_block > GROW_MAX_THREADS / 32 || (c->p.smem_slots & (c->p.smem_slots - 1)) ||
         (c->p.smem_slots > 0 && c->p.smem_slots < 32) || (c->p.mid_slots & (c->p.mid_slots - 1)) ||
         (c->p.mid_slots > 0 && c->p.mid_slots < 32)) {
@@ -398,6 +402,7 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
     for (auto &e : ev) cudaEventCreate(&e);
     Counters *ctr = nullptr;
     i64 *retry_a = nullptr, *retry_b = nullptr;
+    unsigned char *big_seed = nullptr;
     int rc = MSCD_OK;
     cudaEventRecord(ev[0], st);
     do {
@@ -421,6 +426,8 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
         if ((rc = cuda_status(cudaMalloc((void **)&ctr, sizeof(Counters))))) break;
         if ((rc = cuda_status(cudaMalloc((void **)&retry_a, U1 * sizeof(i64))))) break;
         if ((rc = cuda_status(cudaMalloc((void **)&retry_b, U1 * sizeof(i64))))) break;
+        if ((rc = cuda_status(cudaMalloc((void **)&big_seed, (size_t)std::max<i64>(N, 1))))) break;
+        if ((rc = cuda_status(cudaMemsetAsync(big_seed, 0, (size_t)std::max<i64>(N, 1), st)))) break;
         if (c->seeds) {
             if ((rc = cuda_status(cudaMemsetAsync(ctr, 0, sizeof(Counters), st)))) break;
             check_seeds<<<152 * 8, 256, 0, st>>>(c->seeds, N, G.n, &ctr->error_flags); note_launch();
@@ -448,6 +455,11 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
             i64 full = 32;
             while (full < G.n + 1) full <<= 1;
             i64 cg = ladder.back();
+            if (c->p.global_slots > cg && cg < full) {
+                cg = std::min<i64>(c->p.global_slots, full);
+                ladder.push_back((int)cg);
+                in_smem.push_back(false);
+            }
             while (cg < full) {
                 cg = std::min<i64>(cg * 8, full);
                 ladder.push_back((int)cg);
@@ -499,6 +511,7 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
             a.n_retry_out = &ctr->n_retry_out;
             a.error_flags = &ctr->error_flags;
             a.state_bytes = grow_state_bytes(G, cap);
+            a.big_seed = t.cls == 0 ? big_seed : nullptr;
             a.log_kmax = G.kmax > 1 ? (float)std::log((double)G.kmax) : 0.0f;
             i64 *list_dev = nullptr;
             if (!t.all) {
@@ -528,6 +541,11 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
             } else {
                 a.use_smem = 0;
                 const int wpc = GLOBAL_CTA_THREADS / 32;
+                // group bounds (8 bytes per 32 slots and unit) in shared memory when small
+                if (cap <= 16384) {
+                    a.bounds_smem = 1;
+                    smem = (size_t)wpc * 8 * (size_t)(cap / 32);
+                }
                 const size_t budget = (size_t)4 << 30;
                 i64 warps = std::max<i64>(
                     1, std::min<i64>((i64)(budget / a.state_bytes), (i64)c->sm_count * c->p.global_warps_per_sm));
@@ -637,6 +655,7 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
     cudaFree(ctr);
     cudaFree(retry_a);
     cudaFree(retry_b);
+    cudaFree(big_seed);
     for (auto &e : ev) cudaEventDestroy(e);
     if (rc != MSCD_OK && !c->have) free_run(c);
     return rc;

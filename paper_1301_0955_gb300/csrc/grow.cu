@@ -85,7 +85,7 @@ __host__ __device__ __forceinline__ size_t state_bytes_t(int C) {
 }
 
 template <class VT, class HT, bool WEIGHTED>
-__device__ __forceinline__ State<VT, HT, WEIGHTED> carve(unsigned char *base, int C) {
+__device__ __forceinline__ State<VT, HT, WEIGHTED> carve(unsigned char *base, int C, int *bounds) {
     State<VT, HT, WEIGHTED> s;
     s.C = C;
     s.H = 2 * C;
@@ -102,6 +102,10 @@ __device__ __forceinline__ State<VT, HT, WEIGHTED> carve(unsigned char *base, in
     o += 4 * (size_t)(C / 32);
     s.qmax = (int *)(base + o);
     o += 4 * (size_t)(C / 32);
+    if (bounds) {  // group bounds kept apart (shared memory for a global-arena class)
+        s.gmax = bounds;
+        s.qmax = bounds + C / 32;
+    }
     s.hsh = (HT *)(base + o);
     o += 2 * sizeof(HT) * (size_t)C;
     s.flag = base + o;
@@ -312,6 +316,7 @@ __device__ int queue_top(const S &st, Unit &U) {
     for (int iter = 0; iter < 64; ++iter) {
         if (M == ORD_NEG_INF) return best;
         const int othr = ord(unord(M) - 2.0f * U.E2);
+        int mr = ORD_NEG_INF;  // largest refreshed (exact) bound
         for (int base = 0; base < G; base += 32) {
             const int g = base + lane;
             u32 ball = __ballot_sync(FULL_MASK, g < G && st.gmax[g] >= othr);
@@ -323,7 +328,9 @@ __device__ int queue_top(const S &st, Unit &U) {
                 int lb = k == NEG_INF ? -1 : i;
                 float lk = k;
                 warp_best(st, lb, lk, U);
-                if (lane == 0) st.gmax[gg] = lb >= 0 ? ord(lk) : ORD_NEG_INF;
+                const int o = lb >= 0 ? ord(lk) : ORD_NEG_INF;
+                if (lane == 0) st.gmax[gg] = o;
+                mr = max(mr, o);
                 if (lb >= 0 && (best < 0 || ranks_before(st, lb, lk, best, bk, U))) {
                     best = lb;
                     bk = lk;
@@ -331,6 +338,8 @@ __device__ int queue_top(const S &st, Unit &U) {
             }
         }
         __syncwarp();
+        // every other bound is below othr <= M, so an unchanged maximum means done
+        if (mr == M) return best;
         const int M2 = max_bound(st, G);
         if (M2 == M) return best;
         M = M2;
@@ -606,6 +615,15 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
     U.xflags = 0;
     U.ovf = U.err = false;
     int status = MSCD_OK;
+    if (a.big_seed) {
+        // this seed's unit outgrew the class at the previous, finer scale: the
+        // coarser scale's will too (almost always), so hand it on unopened
+        const i64 sc = unit / a.n_seeds;
+        if (sc > 0 && a.alphas[sc - 1] > U.alpha && a.big_seed[si]) {
+            if (lane == 0) a.retry_state[atomicAdd(a.n_retry_state, 1ull)] = unit;
+            return;
+        }
+    }
 
     lookup_insert(st, G, U, U.seed, lane == 0);  // slot 0
     if (lane == 0) st.flag[0] = F_MEMBER;
@@ -661,7 +679,10 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
     if (U.err) {
         if (lane == 0) atomicOr(a.error_flags, 1u);
     } else if (U.ovf) {
-        if (lane == 0) a.retry_state[atomicAdd(a.n_retry_state, 1ull)] = unit;
+        if (lane == 0) {
+            a.retry_state[atomicAdd(a.n_retry_state, 1ull)] = unit;
+            if (a.big_seed) a.big_seed[si] = 1;
+        }
     } else {
         if (status == MSCD_OK && (U.xflags & EXACT_UNDECIDED)) status = MSCD_EUNDECIDED;
         if (!emit(st, a, U, unit, status)) {
@@ -680,7 +701,8 @@ __global__ void __launch_bounds__(MAXT, MINB) grow_kernel(GrowArgs a) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const i64 gw = (i64)blockIdx.x * (blockDim.x >> 5) + wib;
     unsigned char *base = a.use_smem ? smem + (size_t)wib * a.state_bytes : a.gstate + (size_t)gw * a.state_bytes;
-    const State<VT, HT, WEIGHTED> st = carve<VT, HT, WEIGHTED>(base, a.cap);
+    int *bounds = a.bounds_smem ? (int *)smem + (size_t)wib * 2 * (a.cap / 32) : nullptr;
+    const State<VT, HT, WEIGHTED> st = carve<VT, HT, WEIGHTED>(base, a.cap, bounds);
     for (int i = lane; i < st.H; i += 32) st.hsh[i] = 0;
     __syncwarp();
     for (;;) {

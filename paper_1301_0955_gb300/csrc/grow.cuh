@@ -18,6 +18,8 @@ struct GrowArgs {
     // per-warp node-slot state
     int cap;                // node slots per unit (power of 2, >= 32)
     int use_smem;           // 1: dynamic shared memory, 0: global arena
+    int bounds_smem;        // global arena with the group bounds in dynamic shared memory
+    unsigned char *big_seed;  // per seed: outgrew this class at a finer scale (first class only; may be null)
     unsigned char *gstate;  // global arena (warps * state_bytes)
     size_t state_bytes;     // per warp
     i64 max_rounds;

@@ -32,7 +32,7 @@ vp = C.c_void_p
 class mscd_params(C.Structure):
     _fields_ = [("struct_size", C.c_int32), ("warps_per_block", C.c_int32), ("smem_slots", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("mid_slots", C.c_int32), ("global_warps_per_sm", C.c_int32),
-                ("max_rounds", C.c_int64)]
+                ("global_slots", C.c_int32), ("max_rounds", C.c_int64)]
 
 
 class mscd_run_stats(C.Structure):
@@ -129,10 +129,11 @@ class Context:
     """One mscd context on one device."""
 
     def __init__(self, device: int = 0, smem_slots: int = 0, blocks_per_sm: int = 0, max_rounds: int = 0,
-                 warps_per_block: int = 0, mid_slots: int = 0, global_warps_per_sm: int = 0):
+                 warps_per_block: int = 0, mid_slots: int = 0, global_warps_per_sm: int = 0,
+                 global_slots: int = 0):
         L = load()
         p = mscd_params(C.sizeof(mscd_params), warps_per_block, smem_slots, blocks_per_sm, mid_slots,
-                        global_warps_per_sm, max_rounds)
+                        global_warps_per_sm, global_slots, max_rounds)
         h = vp()
         _check(L.mscd_create(C.byref(h), device, C.byref(p)), "mscd_create")
         self.h = h
