@@ -67,6 +67,24 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_max(value, world):
+    """Largest value over the ranks (the whole-job time is the slowest rank's)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, steps, world, max_total_ms):
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * units_per_rank * steps / (max_total_ms / 1e3)
+
+
 def source_hash():
     h = hashlib.sha256()
     for f in GROW_SOURCES:
@@ -273,12 +291,8 @@ def main():
     barrier()
     with ClockSampler(local) as clk:
         times, stats, launches = timed(step_resident, args.steps)
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * units * args.steps / (total_ms / 1e3)
+    total_ms = reduce_max(sum(times), world)
+    value = whole_job_rate(units, args.steps, world, total_ms)
     st = stats[-1]
     grow_ms = statistics.mean(s["ms_grow"] for s in stats)
     alg_bytes = 4.0 * st["edges_scanned"] + 16.0 * (st["units"] + st["adds"] + st["removes"])
