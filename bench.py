@@ -57,6 +57,8 @@ def parse_args():
     p.add_argument("--seeds", type=int, default=0, help="profiling: a seeded sample of this many seeds")
     p.add_argument("--scales", type=int, default=N_SCALES, help="profiling: fewer scales")
     p.add_argument("--flush-mib", type=int, default=1024, help="L2 flush buffer written between steps")
+    p.add_argument("--plain-steps", type=int, default=1,
+                   help="steps of the plain one-launch-per-scale form timed for comparison (0: skip)")
     return p.parse_args()
 
 
@@ -267,7 +269,7 @@ def main():
         d2h_bytes[0] = nb
         ctx.free_graph(gid)
 
-    def timed(step, k):
+    def timed(step, k, c=ctx):
         times = []
         stats = []
         launches = 0
@@ -283,7 +285,7 @@ def main():
             barrier()
             launches += L.mscd_launch_count() - l0
             times.append(e0.elapsed_time(e1))
-            stats.append(ctx.run_stats())
+            stats.append(c.run_stats())
         return times, stats, launches
 
     for _ in range(args.warmup):
@@ -305,6 +307,27 @@ def main():
             traffic = prof.get("dram_bytes_per_step")
     except Exception:
         pass
+    # the plain GPU form: the same kernel, one launch per scale and slot
+    # class, one statically mapped unit per warp (no persistence, no stealing)
+    plain = None
+    if args.plain_steps > 0:
+        ctx_p = mscd.Context(local, schedule=mscd.SCHED_PER_SCALE)
+
+        def step_plain():
+            gid = ctx_p.load_csr(g.n, rp_d, col_d)
+            rc = ctx_p.run(gid, alphas_d, seeds_d, stream=stream)
+            assert rc == mscd.OK, rc
+            ctx_p.free_graph(gid)
+
+        step_plain()
+        pt, pst, _ = timed(step_plain, args.plain_steps, ctx_p)
+        p_ms = reduce_max(sum(pt), world) / args.plain_steps
+        p_grow = statistics.mean(x["ms_grow"] for x in pst)
+        plain = {"schedule": "one launch per scale and slot class, one unit per warp",
+                 "ms_per_step": p_ms, "value": whole_job_rate(units, 1, world, p_ms), "ms_grow": p_grow,
+                 "grow_launches": pst[-1]["grow_launches"], "steps": args.plain_steps,
+                 "speedup_step": p_ms / (total_ms / args.steps), "speedup_grow": p_grow / grow_ms}
+        ctx_p.close()
     e2e = None
     if not args.no_e2e:
         step_e2e()  # warm the host path once
@@ -333,6 +356,7 @@ def main():
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes_per_step": alg_bytes, "kernel_ms_per_step": grow_ms},
             "cpu_baseline": cpu,
+            "plain_per_scale": plain,
             "e2e": e2e,
             "clocks": clk.summary(),
             "gpu_launches": launches,

@@ -88,7 +88,17 @@ typedef struct mscd_params {
     int32_t global_slots;    /* node slots of the first global-arena class (power of 2;
                                 0 = 8 times the last shared-memory class)                */
     int64_t max_rounds;      /* grow/prune repetitions per unit before ETIMEOUT (1e6)     */
+    int32_t schedule;        /* MSCD_SCHED_PERSISTENT (0): every scale's units in one
+                                persistent launch per slot class, warps taking units from a
+                                global counter.  MSCD_SCHED_PER_SCALE (1): the plain form,
+                                one launch per scale and slot class, one unit per warp,
+                                statically mapped (no persistence, no work stealing); the
+                                results are identical, only the speed differs           */
+    int32_t reserved;        /* 0                                                        */
 } mscd_params;
+
+#define MSCD_SCHED_PERSISTENT 0
+#define MSCD_SCHED_PER_SCALE 1
 
 /* Totals of the last run. */
 typedef struct mscd_run_stats {

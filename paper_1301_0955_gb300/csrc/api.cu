@@ -203,6 +203,7 @@ struct Task {
     int cls;                 // index in the node-slot class ladder
     std::vector<i64> units;  // the listed units, unless `all`
     bool all;
+    int scale;               // `all` units of this scale, or of every scale (-1)
 };
 
 }  // namespace
@@ -258,7 +259,8 @@ int mscd_create(mscd_ctx **out, int device, const mscd_params *params) {
     if (c->p.smem_slots < 0) c->p.smem_slots = 0;
     if (c->p.mid_slots < 0) c->p.mid_slots = 0;
     if (c->p.global_warps_per_sm <= 0) c->p.global_warps_per_sm = 16;
-    if (c->p.global_slots < 0 || (c->p.global_slots & (c->p.global_slots - 1))) {
+    if (c->p.global_slots < 0 || (c->p.global_slots & (c->p.global_slots - 1)) ||
+        (c->p.schedule != MSCD_SCHED_PERSISTENT && c->p.schedule != MSCD_SCHED_PER_SCALE)) {
         delete c;
         return MSCD_EINVAL;
     }
@@ -466,8 +468,17 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
                 in_smem.push_back(false);
             }
         }
+        // persistent: one task over every unit; per scale: a task per scale,
+        // each started once the previous scale's classes are done
+        const bool per_scale = c->p.schedule == MSCD_SCHED_PER_SCALE;
         std::vector<Task> tasks;
-        if (U > 0) tasks.push_back(Task{0, {}, true});
+        int next_scale = 0;
+        auto refill = [&]() {
+            if (!tasks.empty() || U == 0 || next_scale >= n_scales) return;
+            tasks.push_back(Task{0, {}, true, per_scale ? next_scale : -1});
+            next_scale = per_scale ? next_scale + 1 : n_scales;
+        };
+        refill();
         unsigned long long cursor = 0;
         size_t free_mem = 0, total_mem = 0;
         cudaMemGetInfo(&free_mem, &total_mem);
@@ -477,7 +488,7 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
             tasks.erase(tasks.begin());
             const int cap = ladder[t.cls];
             const bool sm = in_smem[t.cls];
-            const i64 n_work = t.all ? U : (i64)t.units.size();
+            const i64 n_work = t.all ? (t.scale >= 0 ? N : U) : (i64)t.units.size();
             // room for every list this launch can write (<= min(cap, n) each) when
             // that fits the budget; otherwise units that find it full are retried
             {
@@ -493,6 +504,8 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
             a.n_seeds = N;
             a.n_work = n_work;
             a.work_counter = &ctr->work;
+            a.plain = per_scale ? 1 : 0;
+            a.unit_base = t.all && t.scale >= 0 ? (i64)t.scale * N : 0;
             a.cap = cap;
             a.max_rounds = c->p.max_rounds;
             a.out_nodes = c->out_nodes;
@@ -527,6 +540,7 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
                 break;
             int blocks = 0, threads = 32;
             size_t smem = 0;
+            i64 chunk = n_work;  // work items per launch (the plain form's arena bounds it)
             if (sm) {
                 // as many one-warp units per CTA as fit 220 KiB (<= 16), one CTA per SM
                 a.use_smem = 1;
@@ -549,7 +563,9 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
                 const size_t budget = (size_t)4 << 30;
                 i64 warps = std::max<i64>(
                     1, std::min<i64>((i64)(budget / a.state_bytes), (i64)c->sm_count * c->p.global_warps_per_sm));
-                warps = std::min<i64>(warps, std::max<i64>(n_work, 1));
+                if (per_scale) warps = (i64)(budget / a.state_bytes);
+                warps = std::max<i64>(1, std::min<i64>(warps, std::max<i64>(n_work, 1)));
+                if (per_scale) chunk = warps;
                 threads = (int)std::min<i64>(warps, wpc) * 32;
                 blocks = (int)((warps + threads / 32 - 1) / (threads / 32));
                 if ((rc = ensure_arena(c, (size_t)blocks * (threads / 32) * a.state_bytes))) break;
@@ -560,7 +576,18 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
             cudaEventCreate(&l0);
             cudaEventCreate(&l1);
             cudaEventRecord(l0, st);
-            if ((rc = grow_launch(a, blocks, threads, smem, st))) break;
+            if (!per_scale) {
+                rc = grow_launch(a, blocks, threads, smem, st);
+            } else {
+                // one statically mapped unit per warp: a grid over the items
+                const int wpc = threads / 32;
+                for (i64 b = 0; b < n_work && rc == MSCD_OK; b += chunk) {
+                    a.work_base = b;
+                    const i64 items = std::min<i64>(chunk, n_work - b);
+                    rc = grow_launch(a, (int)((items + wpc - 1) / wpc), threads, smem, st);
+                }
+            }
+            if (rc) break;
             cudaEventRecord(l1, st);
             Counters h{};
             if ((rc = cuda_status(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st)))) break;
@@ -591,7 +618,7 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
                     break;
                 cursor = (unsigned long long)c->out_cap;
                 if ((rc = grow_output(c, c->out_cap + (i64)h.out_needed + (1 << 20), (i64)cursor, st))) break;
-                tasks.insert(tasks.begin(), Task{t.cls, std::move(lst), false});
+                tasks.insert(tasks.begin(), Task{t.cls, std::move(lst), false, t.scale});
             }
             if (h.n_retry_state) {
                 std::vector<i64> lst(h.n_retry_state);
@@ -600,8 +627,9 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
                     break;
                 c->stats.overflow_units += (i64)lst.size();
                 if (t.cls + 1 >= (int)ladder.size()) { rc = MSCD_EDEVICE; break; }
-                tasks.push_back(Task{t.cls + 1, std::move(lst), false});
+                tasks.push_back(Task{t.cls + 1, std::move(lst), false, t.scale});
             }
+            refill();
         }
         if (rc) break;
         cudaEventRecord(ev[1], st);

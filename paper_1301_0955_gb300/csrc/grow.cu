@@ -693,7 +693,8 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
 }
 
 // One unit per warp, persistent: units are taken from a global counter until
-// the work list is exhausted.  State: dynamic shared memory (warp w of the
+// the work list is exhausted (or, in the plain form, one statically mapped
+// unit per warp).  State: dynamic shared memory (warp w of the
 // CTA at w * state_bytes) or the global arena (warp at its global index).
 template <class VT, class HT, bool WEIGHTED, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) grow_kernel(GrowArgs a) {
@@ -705,12 +706,17 @@ __global__ void __launch_bounds__(MAXT, MINB) grow_kernel(GrowArgs a) {
     const State<VT, HT, WEIGHTED> st = carve<VT, HT, WEIGHTED>(base, a.cap, bounds);
     for (int i = lane; i < st.H; i += 32) st.hsh[i] = 0;
     __syncwarp();
+    if (a.plain) {
+        const i64 t = a.work_base + gw;
+        if (t < a.n_work) grow_unit(st, a, a.work_list ? a.work_list[t] : a.unit_base + t);
+        return;
+    }
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(a.work_counter, 1ull);
         t = __shfl_sync(FULL_MASK, t, 0);
         if ((i64)t >= a.n_work) break;
-        const i64 unit = a.work_list ? a.work_list[t] : (i64)t;
+        const i64 unit = a.work_list ? a.work_list[t] : a.unit_base + (i64)t;
         grow_unit(st, a, unit);
     }
 }

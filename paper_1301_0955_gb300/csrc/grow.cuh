@@ -15,6 +15,10 @@ struct GrowArgs {
     const i64 *work_list;
     i64 n_work;
     unsigned long long *work_counter;
+    // plain (non-persistent) form: warp w of the grid takes work item
+    // work_base + w, and unit unit_base + item when there is no list
+    int plain;
+    i64 work_base, unit_base;
     // per-warp node-slot state
     int cap;                // node slots per unit (power of 2, >= 32)
     int use_smem;           // 1: dynamic shared memory, 0: global arena

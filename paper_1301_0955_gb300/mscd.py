@@ -19,6 +19,8 @@ OK = 0
 EINVAL, ENOTSYM, ESELFLOOP, EDUP, ERANGE, ENOMEM, EDEVICE = -1, -2, -3, -4, -5, -6, -7
 ETIMEOUT, ESMALL, EUNDECIDED, EUNSORTED, EWEIGHT, ENORESULT = -8, -9, -10, -11, -12, -13
 DEVICE_PTRS = 1
+SCHED_PERSISTENT = 0
+SCHED_PER_SCALE = 1
 NSTATS = 8
 STAT_FIELDS = ("edges_scanned", "adds", "removes", "rounds", "K", "V", "slow", "undecided")
 
@@ -32,7 +34,8 @@ vp = C.c_void_p
 class mscd_params(C.Structure):
     _fields_ = [("struct_size", C.c_int32), ("warps_per_block", C.c_int32), ("smem_slots", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("mid_slots", C.c_int32), ("global_warps_per_sm", C.c_int32),
-                ("global_slots", C.c_int32), ("max_rounds", C.c_int64)]
+                ("global_slots", C.c_int32), ("max_rounds", C.c_int64), ("schedule", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class mscd_run_stats(C.Structure):
@@ -130,10 +133,10 @@ class Context:
 
     def __init__(self, device: int = 0, smem_slots: int = 0, blocks_per_sm: int = 0, max_rounds: int = 0,
                  warps_per_block: int = 0, mid_slots: int = 0, global_warps_per_sm: int = 0,
-                 global_slots: int = 0):
+                 global_slots: int = 0, schedule: int = 0):
         L = load()
         p = mscd_params(C.sizeof(mscd_params), warps_per_block, smem_slots, blocks_per_sm, mid_slots,
-                        global_warps_per_sm, global_slots, max_rounds)
+                        global_warps_per_sm, global_slots, max_rounds, schedule, 0)
         h = vp()
         _check(L.mscd_create(C.byref(h), device, C.byref(p)), "mscd_create")
         self.h = h

@@ -168,13 +168,15 @@ def test_planted_full_parity(orc, ctx):
 
 
 @pytest.mark.parametrize("weighted", [False, True])
-def test_slot_class_escalation(orc, ctx, weighted):
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_slot_class_escalation(orc, ctx, weighted, schedule):
     """Tiny shared-memory classes force units through every class: two
-    shared-memory classes, then global arenas of growing capacity.  Results
+    shared-memory classes, then global arenas of growing capacity, in the
+    persistent schedule and in the plain one-launch-per-scale form.  Results
     must not change."""
     from paper_1301_0955_gb300 import mscd
 
-    c2 = mscd.Context(0, smem_slots=32, mid_slots=64)
+    c2 = mscd.Context(0, smem_slots=32, mid_slots=64, schedule=schedule)
     g = synth.config_graph(0)
     w = None
     if weighted:
@@ -192,6 +194,8 @@ def test_slot_class_escalation(orc, ctx, weighted):
     assert st["overflow_units"] > 0
     classes = {(l["cap"], l["smem"]) for l in st["launches"]}
     assert (32, 1) in classes and (64, 1) in classes and any(cap > 64 and not sm for cap, sm in classes)
+    if schedule == mscd.SCHED_PER_SCALE:
+        assert st["grow_launches"] >= 3 * len(alphas)
     compare_units(orc, c2, G, alphas, seeds)
     c2.close()
 
