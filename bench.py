@@ -59,6 +59,10 @@ def parse_args():
     p.add_argument("--flush-mib", type=int, default=1024, help="L2 flush buffer written between steps")
     p.add_argument("--plain-steps", type=int, default=1,
                    help="steps of the plain one-launch-per-scale form timed for comparison (0: skip)")
+    p.add_argument("--workload", default="lfr-100k", choices=["lfr-100k", "uneven-batch"])
+    p.add_argument("--batch-graphs", type=int, default=256, help="uneven-batch: number of graphs")
+    p.add_argument("--batch-node-scale", type=float, default=1.0, help="uneven-batch: node count factor")
+    p.add_argument("--batch-scales", type=int, default=16, help="uneven-batch: scales")
     return p.parse_args()
 
 
@@ -154,6 +158,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "samples_under_load": len(load)}
 
 
+def oracle_units(G, alphas, seeds, threads):
+    """One oracle pass (growth + dedup per scale) over `seeds` at every scale;
+    returns (units, seconds, edges scanned)."""
+    import oracle
+
+    m = len(seeds)
+    t0 = time.perf_counter()
+    rc, ptr, nodes, f, st = oracle.run(G, alphas, seeds, threads=threads)
+    for s in range(len(alphas)):
+        lo, hi = s * m, (s + 1) * m
+        oracle.dedup(ptr[lo:hi + 1] - ptr[lo], nodes[ptr[lo]:ptr[hi]])
+    return m * len(alphas), time.perf_counter() - t0, float(st[:, 0].sum())
+
+
 def oracle_sample(g, alphas, seconds, threads):
     """Time the oracle (growth + dedup per scale) on a seeded sample of seeds
     at every scale, sized to about `seconds` of CPU time."""
@@ -164,20 +182,188 @@ def oracle_sample(g, alphas, seconds, threads):
     m = 8
     while True:
         seeds = np.sort(rng.choice(g.n, m, replace=False)).astype(np.int32)
-        t0 = time.perf_counter()
-        rc, ptr, nodes, f, st = oracle.run(G, alphas, seeds, threads=threads)
-        for s in range(len(alphas)):
-            lo, hi = s * m, (s + 1) * m
-            oracle.dedup(ptr[lo:hi + 1] - ptr[lo], nodes[ptr[lo]:ptr[hi]])
-        dt = time.perf_counter() - t0
+        units, dt, edges = oracle_units(G, alphas, seeds, threads)
         if dt >= seconds * 0.5 or m >= g.n:
             break
         m = int(min(g.n, max(2 * m, m * seconds / max(dt, 1e-3) * 0.9)))
-    units = m * len(alphas)
     return {"value": units / dt, "unit": "units/s", "cores": threads, "kind": "oracle",
             "sample": "%d seeds (seeded) x %d scales = %d units of the same workload, oracle growth + dedup on "
                       "%d host threads, %.1f s" % (m, len(alphas), units, threads, dt),
-            "edges_scanned_per_s": float(st[:, 0].sum()) / dt}
+            "edges_scanned_per_s": edges / dt}
+
+
+def oracle_sample_batch(graphs, alphas, seconds, threads):
+    """The same over the batch: seeded parts in turn, a seeded tenth of each
+    part's nodes (at least 8) as seeds, until about `seconds` have passed."""
+    import oracle
+
+    rng = np.random.default_rng(12345)
+    order = rng.permutation(len(graphs))
+    units = 0
+    dt = 0.0
+    edges = 0.0
+    parts = 0
+    for p in order:
+        g = graphs[p]
+        G = oracle.Graph(g.n, g.row_ptr, g.col, g.w)
+        m = min(g.n, max(8, g.n // 10))
+        seeds = np.sort(rng.choice(g.n, m, replace=False)).astype(np.int32)
+        u, t, e = oracle_units(G, alphas, seeds, threads)
+        units += u
+        dt += t
+        edges += e
+        parts += 1
+        if dt >= seconds:
+            break
+    return {"value": units / dt, "unit": "units/s", "cores": threads, "kind": "oracle",
+            "sample": "%d seeded parts of the batch, a seeded tenth of each part's nodes as seeds x %d scales = "
+                      "%d units, oracle growth + dedup on %d host threads, %.1f s" % (parts, len(alphas), units,
+                                                                                      threads, dt),
+            "edges_scanned_per_s": edges / dt}
+
+
+# ---------------------------------------------------------------- workloads
+
+class Lfr100k:
+    """The 100,000-node LFR-style graph, 20 scales, every node a seed."""
+
+    name = "lfr-100k"
+
+    def __init__(self, args):
+        from paper_1301_0955_gb300 import mscd, synth
+
+        self.mscd = mscd
+        self.g = synth.config_graph(1)
+        self.n_scales = args.scales
+        self.alphas = mscd.scales_logspaced(0.5, 1.0, self.n_scales)
+        self.seeds_h = None
+        if args.seeds:
+            self.seeds_h = np.sort(np.random.default_rng(0).choice(self.g.n, args.seeds,
+                                                                   replace=False)).astype(np.int32)
+        n_seeds = self.g.n if self.seeds_h is None else len(self.seeds_h)
+        self.units = self.n_scales * n_seeds
+        self.full = self.seeds_h is None and self.n_scales == N_SCALES
+
+    def config(self):
+        g = self.g
+        return {"workload": WORKLOAD if self.full else
+                "profiling subset: %d seeds x %d scales of the lfr-100k workload"
+                % (self.units // self.n_scales, self.n_scales),
+                "n_nodes": g.n, "nnz": g.nnz, "scales": self.n_scales, "seeds": self.units // self.n_scales}
+
+    def to_device(self, torch, dev):
+        self.rp_d = torch.from_numpy(self.g.row_ptr).to(dev)
+        self.col_d = torch.from_numpy(self.g.col).to(dev)
+        self.alphas_d = torch.from_numpy(self.alphas).to(dev)
+        self.seeds_d = None if self.seeds_h is None else torch.from_numpy(self.seeds_h).to(dev)
+        self.rp_h = torch.from_numpy(self.g.row_ptr).pin_memory().numpy()
+        self.col_h = torch.from_numpy(self.g.col).pin_memory().numpy()
+        self.h2d_bytes = int(self.g.row_ptr.nbytes + self.g.col.nbytes + self.alphas.nbytes)
+
+    def step_resident(self, ctx, stream):
+        gid = ctx.load_csr(self.g.n, self.rp_d, self.col_d)
+        rc = ctx.run(gid, self.alphas_d, self.seeds_d, stream=stream)
+        assert rc == self.mscd.OK, rc
+        ctx.free_graph(gid)
+
+    def step_e2e(self, ctx):
+        gid = ctx.load_csr(self.g.n, self.rp_h, self.col_h)
+        rc = ctx.run(gid, self.alphas, self.seeds_h)
+        assert rc == self.mscd.OK, rc
+        nb = read_results(ctx, self.n_scales, 1)
+        ctx.free_graph(gid)
+        return nb
+
+    step_plain = step_resident
+
+    def cpu_baseline(self, seconds, threads):
+        return oracle_sample(self.g, self.alphas, seconds, threads)
+
+
+class UnevenBatch:
+    """Many independent graphs of uneven size batched as one disjoint union:
+    every seed of every graph at every scale in the same persistent launches."""
+
+    name = "uneven-batch"
+
+    def __init__(self, args):
+        import multiprocessing as mp
+
+        from paper_1301_0955_gb300 import mscd, synth
+
+        self.mscd = mscd
+        specs = synth.uneven_batch_specs(args.batch_graphs, seed=4, scale_nodes=args.batch_node_scale)
+        # generated on the host cores before any GPU call (spawned workers)
+        with mp.get_context("spawn").Pool(min(len(specs), os.cpu_count() or 1)) as pool:
+            self.graphs = pool.map(synth.graph_from_spec, specs, chunksize=1)
+        self.n_scales = args.batch_scales
+        self.alphas = mscd.scales_logspaced(0.5, 1.0, self.n_scales)
+        self.n_total = sum(g.n for g in self.graphs)
+        self.units = self.n_scales * self.n_total
+        self.node_scale = args.batch_node_scale
+
+    def config(self):
+        ns = [g.n for g in self.graphs]
+        return {"workload": "uneven-batch: %d independent two-level LFR-style graphs, node counts log-uniform in "
+                            "[1000, 200000] x %g, mean degree 10-40, mixing 0.2-0.4, unweighted, %d log-spaced "
+                            "scales in [0.5,1], every node a seed, batched as one disjoint union"
+                            % (len(ns), self.node_scale, self.n_scales),
+                "graphs": len(ns), "n_nodes": self.n_total, "nnz": sum(g.nnz for g in self.graphs),
+                "largest_graph": max(ns), "smallest_graph": min(ns), "scales": self.n_scales,
+                "seeds": self.n_total}
+
+    def to_device(self, torch, dev):
+        self.dev_parts = [(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev))
+                          for g in self.graphs]
+        self.alphas_d = torch.from_numpy(self.alphas).to(dev)
+        self.host_parts = [(torch.from_numpy(g.row_ptr).pin_memory().numpy(),
+                            torch.from_numpy(g.col).pin_memory().numpy()) for g in self.graphs]
+        self.h2d_bytes = int(sum(g.row_ptr.nbytes + g.col.nbytes for g in self.graphs) + self.alphas.nbytes)
+
+    def _run(self, ctx, parts, alphas, stream=None):
+        gids = [ctx.load_csr(g.n, rp, col) for g, (rp, col) in zip(self.graphs, parts)]
+        uid = ctx.graph_union(gids)
+        for gid in gids:
+            ctx.free_graph(gid)
+        rc = ctx.run(uid, alphas, None, stream=stream)
+        assert rc == self.mscd.OK, rc
+        return uid
+
+    def step_resident(self, ctx, stream):
+        ctx.free_graph(self._run(ctx, self.dev_parts, self.alphas_d, stream))
+
+    def step_e2e(self, ctx):
+        uid = self._run(ctx, self.host_parts, self.alphas)
+        nb = read_results(ctx, self.n_scales, len(self.graphs))
+        ctx.free_graph(uid)
+        return nb
+
+    def step_plain(self, ctx, stream):
+        """The plain form: graph after graph, one launch per scale and class."""
+        for g, (rp, col) in zip(self.graphs, self.dev_parts):
+            gid = ctx.load_csr(g.n, rp, col)
+            rc = ctx.run(gid, self.alphas_d, None, stream=stream)
+            assert rc == self.mscd.OK, rc
+            ctx.free_graph(gid)
+
+    def cpu_baseline(self, seconds, threads):
+        return oracle_sample_batch(self.graphs, self.alphas, seconds, threads)
+
+
+WORKLOADS = {"lfr-100k": Lfr100k, "uneven-batch": UnevenBatch}
+
+
+def read_results(ctx, n_scales, n_parts):
+    """Device->host read of every scale's communities and every part's
+    stability; returns the bytes read."""
+    nb = 0
+    for s in range(n_scales):
+        ptr, nodes, f, s2c = ctx.communities(s)
+        nb += ptr.nbytes + nodes.nbytes + f.nbytes + s2c.nbytes
+    for p in range(n_parts):
+        nmi, w3, w5 = ctx.stability(part=p)
+        nb += nmi.nbytes + w3.nbytes + w5.nbytes
+    return nb
 
 
 def run_reference(args):
@@ -185,20 +371,20 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    from paper_1301_0955_gb300 import synth
 
-    g = synth.config_graph(1)
-    rc, alphas = oracle.scales_logspaced(0.5, 1.0, N_SCALES)
+    wl = WORKLOADS[args.workload](args)
     threads = os.cpu_count() or 1
     per_step = max(1.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_sample(g, alphas, per_step / 4, threads)
-    vals = [oracle_sample(g, alphas, per_step, threads) for _ in range(args.steps)]
+        wl.cpu_baseline(per_step / 4, threads)
+    vals = [wl.cpu_baseline(per_step, threads) for _ in range(args.steps)]
     v = statistics.median(x["value"] for x in vals)
+    cfg = wl.config()
+    cfg["sample"] = vals[-1]["sample"]
     line = {"impl": "reference", "metric": "seed expansions/s", "value": v, "unit": "units/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64+f128", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": vals[-1]["sample"]},
+            "config": cfg,
             "cpu_baseline": {"value": v, "unit": "units/s", "cores": threads, "kind": "oracle",
                              "sample": vals[-1]["sample"]},
             "e2e": {"value": v, "unit": "units/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -210,33 +396,25 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    world, rank, local = dist_env()
+    wl = WORKLOADS[args.workload](args)  # host-side generation before the first GPU call
     import torch
 
-    world, rank, local = dist_env()
     if world > 1:
         import torch.distributed as dist
 
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_1301_0955_gb300 import build, mscd, synth
+    from paper_1301_0955_gb300 import build, mscd
 
     build.build()
     L = mscd.load()
-    g = synth.config_graph(1)
-    n_scales = args.scales
-    alphas = mscd.scales_logspaced(0.5, 1.0, n_scales)
-    seeds_h = None
-    if args.seeds:
-        seeds_h = np.sort(np.random.default_rng(0).choice(g.n, args.seeds, replace=False)).astype(np.int32)
     ctx = mscd.Context(local)
     stream = torch.cuda.current_stream(dev)
-    rp_d = torch.from_numpy(g.row_ptr).to(dev)
-    col_d = torch.from_numpy(g.col).to(dev)
-    alphas_d = torch.from_numpy(alphas).to(dev)
-    seeds_d = None if seeds_h is None else torch.from_numpy(seeds_h).to(dev)
+    wl.to_device(torch, dev)
     flush = torch.empty(max(1, args.flush_mib) * 256 * 1024, dtype=torch.int32, device=dev)  # > L2 (129 MB)
-    units = n_scales * (g.n if seeds_h is None else len(seeds_h))
+    units = wl.units
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -244,35 +422,11 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    def step_resident():
-        gid = ctx.load_csr(g.n, rp_d, col_d)
-        rc = ctx.run(gid, alphas_d, seeds_d, stream=stream)
-        assert rc == mscd.OK, rc
-        ctx.free_graph(gid)
-
-    # pinned host copies for the end-to-end path
-    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
-    col_h = torch.from_numpy(g.col).pin_memory()
-    rp_hn, col_hn = rp_h.numpy(), col_h.numpy()
-    d2h_bytes = [0]
-
-    def step_e2e():
-        gid = ctx.load_csr(g.n, rp_hn, col_hn)
-        rc = ctx.run(gid, alphas, seeds_h)
-        assert rc == mscd.OK, rc
-        nb = 0
-        for s in range(n_scales):
-            ptr, nodes, f, s2c = ctx.communities(s)
-            nb += ptr.nbytes + nodes.nbytes + f.nbytes + s2c.nbytes
-        nmi, w3, w5 = ctx.stability()
-        nb += nmi.nbytes + w3.nbytes + w5.nbytes
-        d2h_bytes[0] = nb
-        ctx.free_graph(gid)
-
-    def timed(step, k, c=ctx):
+    def timed(step, k, c):
         times = []
         stats = []
         launches = 0
+        out = None
         for _ in range(k):
             flush.zero_()
             barrier()
@@ -280,19 +434,20 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step()
+            out = step(c)
             e1.record(stream)
             barrier()
             launches += L.mscd_launch_count() - l0
             times.append(e0.elapsed_time(e1))
             stats.append(c.run_stats())
-        return times, stats, launches
+        return times, stats, launches, out
 
+    resident = lambda c: wl.step_resident(c, stream)  # noqa: E731
     for _ in range(args.warmup):
-        step_resident()
+        resident(ctx)
     barrier()
     with ClockSampler(local) as clk:
-        times, stats, launches = timed(step_resident, args.steps)
+        times, stats, launches, _ = timed(resident, args.steps, ctx)
     total_ms = reduce_max(sum(times), world)
     value = whole_job_rate(units, args.steps, world, total_ms)
     st = stats[-1]
@@ -303,7 +458,7 @@ def main():
     traffic = None
     try:
         prof = json.load(open(PROFILE_FILE))
-        if prof.get("source_hash") == source_hash():
+        if prof.get("source_hash") == source_hash() and prof.get("workload") == wl.name:
             traffic = prof.get("dram_bytes_per_step")
     except Exception:
         pass
@@ -312,42 +467,38 @@ def main():
     plain = None
     if args.plain_steps > 0:
         ctx_p = mscd.Context(local, schedule=mscd.SCHED_PER_SCALE)
-
-        def step_plain():
-            gid = ctx_p.load_csr(g.n, rp_d, col_d)
-            rc = ctx_p.run(gid, alphas_d, seeds_d, stream=stream)
-            assert rc == mscd.OK, rc
-            ctx_p.free_graph(gid)
-
-        step_plain()
-        pt, pst, _ = timed(step_plain, args.plain_steps, ctx_p)
+        plain_step = lambda c: wl.step_plain(c, stream)  # noqa: E731
+        plain_step(ctx_p)
+        pt, pst, _, _ = timed(plain_step, args.plain_steps, ctx_p)
         p_ms = reduce_max(sum(pt), world) / args.plain_steps
-        p_grow = statistics.mean(x["ms_grow"] for x in pst)
-        plain = {"schedule": "one launch per scale and slot class, one unit per warp",
-                 "ms_per_step": p_ms, "value": whole_job_rate(units, 1, world, p_ms), "ms_grow": p_grow,
-                 "grow_launches": pst[-1]["grow_launches"], "steps": args.plain_steps,
-                 "speedup_step": p_ms / (total_ms / args.steps), "speedup_grow": p_grow / grow_ms}
+        plain = {"schedule": "one launch per scale and slot class, one unit per warp"
+                             + (", graph after graph" if wl.name == "uneven-batch" else ""),
+                 "ms_per_step": p_ms, "value": whole_job_rate(units, 1, world, p_ms),
+                 "steps": args.plain_steps, "speedup_step": p_ms / (total_ms / args.steps)}
+        if wl.name != "uneven-batch":
+            p_grow = statistics.mean(x["ms_grow"] for x in pst)
+            plain.update({"ms_grow": p_grow, "grow_launches": pst[-1]["grow_launches"],
+                          "speedup_grow": p_grow / grow_ms})
         ctx_p.close()
     e2e = None
     if not args.no_e2e:
-        step_e2e()  # warm the host path once
-        et, _, _ = timed(step_e2e, max(1, min(args.steps, 2)))
+        wl.step_e2e(ctx)  # warm the host path once
+        et, _, _, d2h = timed(lambda c: wl.step_e2e(c), max(1, min(args.steps, 2)), ctx)
         e2e = {"value": units / (statistics.mean(et) / 1e3), "unit": "units/s",
-               "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes + alphas.nbytes),
-               "d2h_bytes_per_step": int(d2h_bytes[0]), "ms_per_step": statistics.mean(et)}
+               "h2d_bytes_per_step": wl.h2d_bytes, "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": statistics.mean(et)}
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and seeds_h is None:
-        cpu = oracle_sample(g, alphas, args.cpu_seconds, os.cpu_count() or 1)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and getattr(wl, "full", True):
+        cpu = wl.cpu_baseline(args.cpu_seconds, os.cpu_count() or 1)
     if rank == 0:
+        cfg = wl.config()
+        cfg.update({"units_per_step_per_gpu": units, "l2": "flushed between steps (%d MiB write)" % args.flush_mib,
+                    "parallelism": "replicas" if world > 1 else "single"})
         line = {
             "metric": "seed expansions/s", "value": value, "unit": "units/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if seeds_h is None and n_scales == N_SCALES else
-                       "profiling subset: %d seeds x %d scales of the lfr-100k workload" % (units // n_scales, n_scales),
-                       "n_nodes": g.n, "nnz": g.nnz, "scales": n_scales, "seeds": units // n_scales,
-                       "units_per_step_per_gpu": units, "l2": "flushed between steps (%d MiB write)" % args.flush_mib,
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": cfg,
             "edges_scanned_per_s": world * st["edges_scanned"] * args.steps / (total_ms / 1e3),
             "stage_ms": {k: st[k] for k in ("ms_grow", "ms_dedup", "ms_stability", "ms_total")},
             "run_stats": {k: st[k] for k in ("units", "edges_scanned", "adds", "removes", "slow_decisions",

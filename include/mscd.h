@@ -100,6 +100,10 @@ typedef struct mscd_params {
 #define MSCD_SCHED_PERSISTENT 0
 #define MSCD_SCHED_PER_SCALE 1
 
+/* mscd_autotune flags */
+#define MSCD_TUNE_APPLY 1u   /* make the result the context's parameters          */
+#define MSCD_TUNE_CACHED 2u  /* reuse a result for the same graph shape if present */
+
 /* Totals of the last run. */
 typedef struct mscd_run_stats {
     int64_t units;            /* (scale, seed) units grown                         */
@@ -152,6 +156,26 @@ int mscd_graph_load_csr(mscd_ctx *ctx, int64_t n, const int64_t *row_ptr, const 
 /* Release a resident graph.  EINVAL for an unknown id. */
 int mscd_graph_free(mscd_ctx *ctx, int32_t graph_id);
 
+/* Batching of independent graphs.  Every community grows on its own from its
+ * seed (Alg. 1), so many graphs form one problem: the disjoint union of the
+ * resident graphs graph_ids[0..n_parts) becomes a new resident graph whose
+ * node ids are those of part p shifted by the node counts of the parts before
+ * it (offsets from mscd_graph_parts).  A run on it grows every seed of every
+ * part in the same launches; the deduplicated communities of a scale are the
+ * parts' communities one after another; the stability is per part
+ * (mscd_get_stability_part: the NMI of Sec. 4 with n = the part's node count).
+ * Results per part equal those of the part run alone.  The parts stay resident
+ * and owned by the caller (the union holds copies).  EINVAL: an unknown id, a
+ * part that is itself a union, weighted and unweighted parts mixed; ERANGE:
+ * 2^31 - 1 nodes or more, or a total volume of 2^62 weight units or more once
+ * weighted parts share the smallest weight unit. */
+int mscd_graph_union(mscd_ctx *ctx, const int32_t *graph_ids, int32_t n_parts, int32_t *union_id);
+
+/* Part node offsets of a resident graph: node_offset int64[n_parts+1] (cap
+ * entries); a graph loaded from one CSR is one part {0, n}.  ESMALL with
+ * *n_parts set when cap < n_parts + 1. */
+int mscd_graph_parts(mscd_ctx *ctx, int32_t graph_id, int64_t *node_offset, int32_t cap, int32_t *n_parts);
+
 /* Facts of a resident graph: node and entry counts, the weight unit 2^unit_exp
  * of the exact fixed-point weights, total volume in weight units. */
 int mscd_graph_info(mscd_ctx *ctx, int32_t graph_id, int64_t *n, int64_t *nnz, int32_t *unit_exp,
@@ -199,12 +223,34 @@ int mscd_get_communities(mscd_ctx *ctx, int32_t scale_idx, int64_t *ptr, int64_t
                          int64_t nodes_cap, double *fitness, int32_t *seed2comm, int64_t *n_comms,
                          int64_t *n_nodes);
 
+/* Autotuner (no counterpart in the paper, whose growth runs one community
+ * per CPU thread).  Times the growth alone on n_sample evenly spaced seeds of
+ * graph_id (0 = min(n, 20000)) at the given scales under candidate schedules
+ * and keeps the fastest: the node-slot capacity of the shared-memory class
+ * (256..2048), of the first global-arena class (4096..16384, or 8 times the
+ * first), and the resident units per SM of the global-arena classes (8..32),
+ * searched one coordinate at a time from the context's current parameters.
+ * The results of a run do not depend on any of these (only its speed).  The
+ * winner goes to *best (may be NULL) with its growth time on the sample in
+ * *best_ms (may be NULL), into a per-context cache keyed by the graph's shape
+ * (log2 n, weighted, degree width), and with MSCD_TUNE_APPLY into the context's
+ * parameters; MSCD_TUNE_CACHED returns a cached result without timing.  Clears
+ * the context's last run (MSCD_ENORESULT for the getters until the next run).
+ * alphas is a host array. */
+int mscd_autotune(mscd_ctx *ctx, int32_t graph_id, const double *alphas, int32_t n_scales, int64_t n_sample,
+                  uint32_t flags, mscd_params *best, double *best_ms);
+
 /* Stability across scales (Sec. 4): nmi_succ double[n_scales-1] with the
  * overlapping NMI between deduplicated sets of scales i and i+1; nmi_win3 and
  * nmi_win5 double[n_scales] with its mean over the window of 3 (5) scales
  * centred on scale i (clipped at the ends; NaN when the window holds no pair).
  * Any pointer may be NULL. */
 int mscd_get_stability(mscd_ctx *ctx, double *nmi_succ, double *nmi_win3, double *nmi_win5);
+
+/* The same for part `part` of a union graph (mscd_graph_union); part 0 is what
+ * mscd_get_stability returns.  A part without seeds in the run gets NaN.
+ * EINVAL for a part outside the last run's graph. */
+int mscd_get_stability_part(mscd_ctx *ctx, int32_t part, double *nmi_succ, double *nmi_win3, double *nmi_win5);
 
 /* Totals of the last run. */
 int mscd_get_run_stats(mscd_ctx *ctx, mscd_run_stats *out);

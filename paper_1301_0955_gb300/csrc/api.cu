@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <map>
 #include <vector>
 
 #include "common.cuh"
@@ -27,6 +28,10 @@ struct GraphRec {
     i64 *wfx = nullptr, *k = nullptr;
     float *logk = nullptr;
     DevGraph g;
+    // a disjoint union of parts (mscd_graph_union): node offsets, host and device
+    std::vector<i64> parts;
+    i64 *part_off = nullptr;  // null for a graph loaded from one CSR
+    i64 max_part_n = 0;       // largest part (= n for one CSR): bounds a community's size
 };
 
 struct Counters {
@@ -64,6 +69,12 @@ __global__ void sum_unit_stats(const i64 *ustat, const i32 *ulen, const i32 *ust
         for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
         if ((threadIdx.x & 31) == 0 && v) atomicAdd(&tot[j], v);
     }
+}
+
+// After a scale's dedup: unit j's list is its community's list.
+__global__ void point_units(const i32 *seed2comm, const i64 *comm_ptr, i64 N, i64 *uoff) {
+    for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (i64)gridDim.x * blockDim.x)
+        uoff[j] = comm_ptr[seed2comm[j]];
 }
 
 __global__ void gather_lists(const i64 *uoff, const i32 *ulen, const i64 *dst_ptr, const i32 *nodes, i64 N,
@@ -108,8 +119,11 @@ struct mscd_ctx {
     i32 *out_nodes = nullptr;
     i64 out_cap = 0;
     std::vector<ScaleResult> scales;
-    std::vector<double> nmi_succ, win3, win5;
+    int32_t n_parts = 1;
+    std::vector<double> nmi_succ, win3, win5;  // per part: S-1, S and S values
     mscd_run_stats stats{};
+    // autotuner results by graph shape class: parameters and growth ms of the sample
+    std::map<u64, std::pair<mscd_params, double>> tune_cache;
     // reusable growth arena
     unsigned char *arena = nullptr;
     size_t arena_bytes = 0;
@@ -149,8 +163,11 @@ void free_graph(GraphRec &g) {
     cudaFree(g.wfx);
     cudaFree(g.k);
     cudaFree(g.logk);
+    cudaFree(g.part_off);
     g = GraphRec{};
 }
+
+int add_graph(mscd_ctx *c, const GraphRec &g, int32_t *graph_id);
 
 GraphRec *find_graph(mscd_ctx *c, int32_t id) {
     if (!c || id < 0 || id >= (int32_t)c->graphs.size() || !c->graphs[id].live) return nullptr;
@@ -201,9 +218,8 @@ void window_means(const std::vector<double> &nmi, int32_t S, int p, std::vector<
 
 struct Task {
     int cls;                 // index in the node-slot class ladder
-    std::vector<i64> units;  // the listed units, unless `all`
+    std::vector<i64> units;  // the listed units, unless `all` (every unit of the scale group)
     bool all;
-    int scale;               // `all` units of this scale, or of every scale (-1)
 };
 
 }  // namespace
@@ -324,6 +340,52 @@ int mscd_graph_load_csr(mscd_ctx *c, int64_t n, const int64_t *row_ptr, const in
     cudaFree(g.w);  // the exact fixed-point copy replaces it
     g.w = nullptr;
     g.live = true;
+    g.parts = {0, n};
+    g.max_part_n = n;
+    return add_graph(c, g, graph_id);
+}
+
+int mscd_graph_union(mscd_ctx *c, const int32_t *graph_ids, int32_t n_parts, int32_t *union_id) {
+    if (!c || !graph_ids || n_parts < 1 || !union_id) return MSCD_EINVAL;
+    std::vector<DevGraph> parts;
+    i64 max_part = 0;
+    for (int32_t i = 0; i < n_parts; ++i) {
+        GraphRec *r = find_graph(c, graph_ids[i]);
+        if (!r || r->part_off) return MSCD_EINVAL;  // parts are graphs loaded from one CSR
+        parts.push_back(r->g);
+        max_part = std::max(max_part, r->g.n);
+    }
+    MSCD_CUDA(cudaSetDevice(c->device));
+    GraphRec g;
+    int rc = graph_union(parts, &g.g, &g.rp, &g.col, &g.wfx, &g.k, &g.logk, &g.parts, c->own);
+    if (rc) return rc;
+    rc = cuda_status(cudaMalloc((void **)&g.part_off, g.parts.size() * sizeof(i64)));
+    if (!rc)
+        rc = cuda_status(cudaMemcpy(g.part_off, g.parts.data(), g.parts.size() * sizeof(i64), cudaMemcpyHostToDevice));
+    if (rc) {
+        free_graph(g);
+        return rc;
+    }
+    g.max_part_n = max_part;
+    g.live = true;
+    return add_graph(c, g, union_id);
+}
+
+int mscd_graph_parts(mscd_ctx *c, int32_t graph_id, int64_t *node_offset, int32_t cap, int32_t *n_parts) {
+    GraphRec *g = find_graph(c, graph_id);
+    if (!g || !n_parts || cap < 0 || (cap > 0 && !node_offset)) return MSCD_EINVAL;
+    const int32_t P = (int32_t)g->parts.size() - 1;
+    *n_parts = P;
+    if (cap < P + 1) return MSCD_ESMALL;
+    std::copy(g->parts.begin(), g->parts.end(), node_offset);
+    return MSCD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int add_graph(mscd_ctx *c, const GraphRec &g, int32_t *graph_id) {
     int32_t id = -1;
     for (size_t i = 0; i < c->graphs.size(); ++i)
         if (!c->graphs[i].live) {
@@ -339,6 +401,10 @@ int mscd_graph_load_csr(mscd_ctx *c, int64_t n, const int64_t *row_ptr, const in
     *graph_id = id;
     return MSCD_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int mscd_graph_free(mscd_ctx *c, int32_t graph_id) {
     GraphRec *g = find_graph(c, graph_id);
@@ -378,8 +444,13 @@ int mscd_scales_logspaced(double vmin, double a, int32_t x, double *out) {
     return MSCD_OK;
 }
 
-int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scales, const int32_t *seeds,
-             int64_t n_seeds, uint32_t flags, void *cuda_stream) {
+}  // extern "C"
+
+namespace {
+
+// The whole path of mscd_run; growth_only stops after the growth (autotuning).
+int run_impl(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scales, const int32_t *seeds,
+             int64_t n_seeds, uint32_t flags, void *cuda_stream, bool growth_only) {
     GraphRec *gr = find_graph(c, graph_id);
     if (!gr || !alphas || n_scales < 1) return MSCD_EINVAL;
     MSCD_CUDA(cudaSetDevice(c->device));
@@ -402,6 +473,7 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
     const i64 U = c->U;
     cudaEvent_t ev[4];
     for (auto &e : ev) cudaEventCreate(&e);
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> dedup_ev;  // around each group's dedup
     Counters *ctr = nullptr;
     i64 *retry_a = nullptr, *retry_b = nullptr;
     unsigned char *big_seed = nullptr;
@@ -450,12 +522,17 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
             const size_t smem_budget = 220 * 1024;
             int c0 = c->p.smem_slots;
             if (c0 == 0) c0 = grow_state_bytes(G, 1024) * 4 <= smem_budget ? 1024 : 512;
+            if (grow_state_bytes(G, c0) > smem_budget) {  // one unit's slots must fit a CTA
+                rc = MSCD_EINVAL;
+                break;
+            }
             ladder.push_back(c0);
             if (c->p.mid_slots > ladder.back() && grow_state_bytes(G, c->p.mid_slots) <= smem_budget)
                 ladder.push_back(c->p.mid_slots);
             in_smem.assign(ladder.size(), true);
+            // a community stays inside its seed's part: the part size bounds it
             i64 full = 32;
-            while (full < G.n + 1) full <<= 1;
+            while (full < gr->max_part_n + 1) full <<= 1;
             i64 cg = ladder.back();
             if (c->p.global_slots > cg && cg < full) {
                 cg = std::min<i64>(c->p.global_slots, full);
@@ -468,31 +545,40 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
                 in_smem.push_back(false);
             }
         }
-        // persistent: one task over every unit; per scale: a task per scale,
-        // each started once the previous scale's classes are done
+        // Scale groups.  The member lists of a group's units go to one output
+        // buffer; once the group is grown, each of its scales is deduplicated
+        // and its units are pointed at their community's list (the lists are
+        // equal), so the buffer is free again for the next group.  A group is
+        // as many scales as fit a quarter of the free memory at the expected
+        // list length (the last group's mean, with a margin); the persistent
+        // schedule usually needs one group, the plain form takes one scale at
+        // a time.  Within a group: a task list of (slot class, units).
         const bool per_scale = c->p.schedule == MSCD_SCHED_PER_SCALE;
-        std::vector<Task> tasks;
-        int next_scale = 0;
-        auto refill = [&]() {
-            if (!tasks.empty() || U == 0 || next_scale >= n_scales) return;
-            tasks.push_back(Task{0, {}, true, per_scale ? next_scale : -1});
-            next_scale = per_scale ? next_scale + 1 : n_scales;
-        };
-        refill();
-        unsigned long long cursor = 0;
         size_t free_mem = 0, total_mem = 0;
         cudaMemGetInfo(&free_mem, &total_mem);
         const i64 out_budget = (i64)(free_mem / 4 / sizeof(i32));  // output may take a quarter of free memory
+        double per_unit = std::max(1.0, std::min<double>(256.0, (double)gr->max_part_n));
+        int32_t s0 = 0;
+        while (s0 < n_scales && rc == MSCD_OK) {
+        int32_t s1 = s0 + 1;
+        if (!per_scale && N > 0)
+            s1 = (int32_t)std::min<i64>(n_scales, s0 + std::max<i64>(1, (i64)(out_budget / (per_unit * N))));
+        else if (!per_scale)
+            s1 = n_scales;
+        const i64 group_units = (i64)(s1 - s0) * N;
+        std::vector<Task> tasks;
+        if (group_units > 0) tasks.push_back(Task{0, {}, true});
+        unsigned long long cursor = 0;
         while (!tasks.empty() && rc == MSCD_OK) {
             Task t = std::move(tasks.front());
             tasks.erase(tasks.begin());
             const int cap = ladder[t.cls];
             const bool sm = in_smem[t.cls];
-            const i64 n_work = t.all ? (t.scale >= 0 ? N : U) : (i64)t.units.size();
+            const i64 n_work = t.all ? group_units : (i64)t.units.size();
             // room for every list this launch can write (<= min(cap, n) each) when
             // that fits the budget; otherwise units that find it full are retried
             {
-                const i64 bound = (i64)cursor + n_work * std::min<i64>(cap, std::max<i64>(G.n, 1));
+                const i64 bound = (i64)cursor + n_work * std::min<i64>(cap, std::max<i64>(gr->max_part_n, 1));
                 const i64 want = std::min<i64>(bound, std::max<i64>(out_budget, (i64)cursor + n_work * 64));
                 if ((rc = grow_output(c, want, (i64)cursor, st))) break;
             }
@@ -505,7 +591,7 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
             a.n_work = n_work;
             a.work_counter = &ctr->work;
             a.plain = per_scale ? 1 : 0;
-            a.unit_base = t.all && t.scale >= 0 ? (i64)t.scale * N : 0;
+            a.unit_base = t.all ? (i64)s0 * N : 0;
             a.cap = cap;
             a.max_rounds = c->p.max_rounds;
             a.out_nodes = c->out_nodes;
@@ -618,7 +704,7 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
                     break;
                 cursor = (unsigned long long)c->out_cap;
                 if ((rc = grow_output(c, c->out_cap + (i64)h.out_needed + (1 << 20), (i64)cursor, st))) break;
-                tasks.insert(tasks.begin(), Task{t.cls, std::move(lst), false, t.scale});
+                tasks.insert(tasks.begin(), Task{t.cls, std::move(lst), false});
             }
             if (h.n_retry_state) {
                 std::vector<i64> lst(h.n_retry_state);
@@ -627,10 +713,32 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
                     break;
                 c->stats.overflow_units += (i64)lst.size();
                 if (t.cls + 1 >= (int)ladder.size()) { rc = MSCD_EDEVICE; break; }
-                tasks.push_back(Task{t.cls + 1, std::move(lst), false, t.scale});
+                tasks.push_back(Task{t.cls + 1, std::move(lst), false});
             }
-            refill();
         }
+        if (rc) break;
+        if (group_units > 0)
+            per_unit = std::max(per_unit, 1.25 * (double)cursor / (double)group_units);
+        if (!growth_only) {
+            // dedup the group's scales; point their units at the community lists
+            cudaEvent_t d0, d1;
+            cudaEventCreate(&d0);
+            cudaEventCreate(&d1);
+            dedup_ev.push_back({d0, d1});
+            cudaEventRecord(d0, st);
+            c->scales.resize(n_scales);
+            for (int32_t s = s0; s < s1 && rc == MSCD_OK; ++s) {
+                rc = dedup_scale(c->uoff + s * N, c->ulen + s * N, c->uhash + s * N, c->uf + s * N, c->out_nodes, N,
+                                 &c->scales[s], st);
+                if (rc == MSCD_OK && N > 0) {
+                    point_units<<<152 * 4, 256, 0, st>>>(c->scales[s].seed2comm, c->scales[s].comm_ptr, N,
+                                                          c->uoff + s * N); note_launch();
+                }
+            }
+            cudaEventRecord(d1, st);
+        }
+        s0 = s1;
+        }  // scale groups
         if (rc) break;
         cudaEventRecord(ev[1], st);
         // ---- totals ----
@@ -650,27 +758,52 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
         c->stats.undecided = (i64)ht[4];
         c->stats.member_entries = (i64)ht[7];
         const i64 n_timeout = (i64)ht[5], n_undecided = (i64)ht[6];
-        // ---- dedup per scale ----
-        c->scales.resize(n_scales);
-        for (int32_t s = 0; s < n_scales && rc == MSCD_OK; ++s)
-            rc = dedup_scale(c->uoff + s * N, c->ulen + s * N, c->uhash + s * N, c->uf + s * N, c->out_nodes, N,
-                             &c->scales[s], st);
-        if (rc) break;
+        if (growth_only) {
+            cudaEventRecord(ev[2], st);
+            cudaEventRecord(ev[3], st);
+            if ((rc = cuda_status(cudaEventSynchronize(ev[3])))) break;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            c->stats.ms_grow = c->stats.ms_total = ms;
+            if (n_undecided) rc = MSCD_EUNDECIDED;
+            else if (n_timeout) rc = MSCD_ETIMEOUT;
+            break;
+        }
         cudaEventRecord(ev[2], st);
         // ---- stability ----
-        c->nmi_succ.assign(std::max(n_scales - 1, 0), NAN);
-        for (int32_t s = 0; s + 1 < n_scales && rc == MSCD_OK; ++s)
-            rc = nmi_between(c->scales[s], c->scales[s + 1], G.n, &c->nmi_succ[s], st);
+        // per part: successive-scale NMI and window means
+        const int32_t P = (int32_t)gr->parts.size() - 1;
+        const int32_t S1 = std::max(n_scales - 1, 0);
+        c->n_parts = P;
+        c->nmi_succ.assign((size_t)P * S1, NAN);
+        {
+            std::vector<double> pn(P);
+            for (int32_t s = 0; s + 1 < n_scales && rc == MSCD_OK; ++s) {
+                rc = nmi_between(c->scales[s], c->scales[s + 1], G.n, gr->part_off, P, pn.data(), st);
+                for (int32_t p = 0; p < P; ++p) c->nmi_succ[(size_t)p * S1 + s] = pn[p];
+            }
+        }
         if (rc) break;
-        window_means(c->nmi_succ, n_scales, 3, c->win3);
-        window_means(c->nmi_succ, n_scales, 5, c->win5);
+        c->win3.assign((size_t)P * n_scales, NAN);
+        c->win5.assign((size_t)P * n_scales, NAN);
+        for (int32_t p = 0; p < P; ++p) {
+            std::vector<double> one(c->nmi_succ.begin() + (size_t)p * S1, c->nmi_succ.begin() + (size_t)(p + 1) * S1);
+            std::vector<double> w;
+            window_means(one, n_scales, 3, w);
+            std::copy(w.begin(), w.end(), c->win3.begin() + (size_t)p * n_scales);
+            window_means(one, n_scales, 5, w);
+            std::copy(w.begin(), w.end(), c->win5.begin() + (size_t)p * n_scales);
+        }
         cudaEventRecord(ev[3], st);
         if ((rc = cuda_status(cudaEventSynchronize(ev[3])))) break;
-        float ms = 0;
+        float ms = 0, md = 0;
+        for (auto &d : dedup_ev) {
+            cudaEventElapsedTime(&ms, d.first, d.second);
+            md += ms;
+        }
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        c->stats.ms_grow = ms;
-        cudaEventElapsedTime(&ms, ev[1], ev[2]);
-        c->stats.ms_dedup = ms;
+        c->stats.ms_grow = ms - md;  // growth with its totals, the dedup of the groups taken out
+        c->stats.ms_dedup = md;
         cudaEventElapsedTime(&ms, ev[2], ev[3]);
         c->stats.ms_stability = ms;
         cudaEventElapsedTime(&ms, ev[0], ev[3]);
@@ -685,8 +818,93 @@ int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
     cudaFree(retry_b);
     cudaFree(big_seed);
     for (auto &e : ev) cudaEventDestroy(e);
+    for (auto &d : dedup_ev) {
+        cudaEventDestroy(d.first);
+        cudaEventDestroy(d.second);
+    }
     if (rc != MSCD_OK && !c->have) free_run(c);
     return rc;
+}
+
+// Graph shape class of the autotuner's cache: size (log2 n), weighted, slot width.
+u64 tune_key(const DevGraph &g) {
+    int lg = 0;
+    while (lg < 62 && ((i64)1 << lg) < g.n) ++lg;
+    return (u64)lg | (g.wfx ? 1ull << 8 : 0ull) | (g.kmax < 65536 ? 1ull << 9 : 0ull);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scales, const int32_t *seeds,
+             int64_t n_seeds, uint32_t flags, void *cuda_stream) {
+    return run_impl(c, graph_id, alphas, n_scales, seeds, n_seeds, flags, cuda_stream, false);
+}
+
+int mscd_autotune(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scales, int64_t n_sample,
+                  uint32_t flags, mscd_params *best, double *best_ms) {
+    GraphRec *gr = find_graph(c, graph_id);
+    if (!gr || !alphas || n_scales < 1 || n_sample < 0) return MSCD_EINVAL;
+    const u64 key = tune_key(gr->g);
+    if ((flags & MSCD_TUNE_CACHED) && c->tune_cache.count(key)) {
+        const mscd_params &p = c->tune_cache[key].first;
+        if (best) *best = p;
+        if (best_ms) *best_ms = c->tune_cache[key].second;
+        if (flags & MSCD_TUNE_APPLY) c->p = p;
+        return MSCD_OK;
+    }
+    // evenly spaced seeds over the graph (every part of a union alike)
+    const i64 n = gr->g.n;
+    const i64 m = std::min<i64>(n, n_sample > 0 ? n_sample : 20000);
+    if (m < 1) return MSCD_EINVAL;
+    std::vector<i32> seeds(m);
+    for (i64 i = 0; i < m; ++i) seeds[i] = (i32)((__int128)i * n / m);
+    const mscd_params saved = c->p;
+    mscd_params cur = c->p;
+    int rc = MSCD_OK;
+    auto time_it = [&](const mscd_params &p, double *ms) -> int {
+        c->p = p;
+        int r = run_impl(c, graph_id, alphas, n_scales, seeds.data(), m, 0, nullptr, true);
+        *ms = c->stats.ms_grow;
+        return r;
+    };
+    double cur_ms = 0.0, ms = 0.0;
+    if ((rc = time_it(cur, &cur_ms))) {  // also the warm-up
+        c->p = saved;
+        free_run(c);
+        return rc;
+    }
+    if ((rc = time_it(cur, &cur_ms)) == MSCD_OK) {
+        // coordinate search: first shared-memory class, first global class, global residency
+        const int smem_c[] = {256, 512, 1024, 2048};
+        const int glob_c[] = {0, 4096, 8192, 16384};
+        const int warps_c[] = {8, 12, 16, 24, 32};
+        for (int axis = 0; axis < 3 && rc == MSCD_OK; ++axis) {
+            const int count = axis == 0 ? 4 : axis == 1 ? 4 : 5;
+            for (int i = 0; i < count && rc == MSCD_OK; ++i) {
+                mscd_params p = cur;
+                if (axis == 0) p.smem_slots = smem_c[i];
+                if (axis == 1) p.global_slots = glob_c[i];
+                if (axis == 2) p.global_warps_per_sm = warps_c[i];
+                if (axis == 1 && p.global_slots && p.global_slots <= std::max(p.smem_slots, 1024)) continue;
+                if (std::memcmp(&p, &cur, sizeof(p)) == 0) continue;
+                if ((rc = time_it(p, &ms))) break;
+                if (ms < cur_ms) {
+                    cur = p;
+                    cur_ms = ms;
+                }
+            }
+        }
+    }
+    free_run(c);
+    c->p = saved;
+    if (rc) return rc;
+    c->tune_cache[key] = {cur, cur_ms};
+    if (flags & MSCD_TUNE_APPLY) c->p = cur;
+    if (best) *best = cur;
+    if (best_ms) *best_ms = cur_ms;
+    return MSCD_OK;
 }
 
 int mscd_get_membership(mscd_ctx *c, int32_t scale_idx, int64_t seed_idx, int32_t *buf, int64_t cap, int64_t *len,
@@ -703,7 +921,9 @@ int mscd_get_membership(mscd_ctx *c, int32_t scale_idx, int64_t seed_idx, int32_
     if (fitness) MSCD_CUDA(cudaMemcpy(fitness, c->uf + u, sizeof(double), cudaMemcpyDeviceToHost));
     *len = m;
     if (cap < m || (m > 0 && !buf)) return MSCD_ESMALL;
-    if (m > 0) MSCD_CUDA(cudaMemcpy(buf, c->out_nodes + off, (size_t)m * sizeof(i32), cudaMemcpyDeviceToHost));
+    if (m > 0)
+        MSCD_CUDA(cudaMemcpy(buf, c->scales[scale_idx].comm_nodes + off, (size_t)m * sizeof(i32),
+                             cudaMemcpyDeviceToHost));
     return MSCD_OK;
 }
 
@@ -737,7 +957,8 @@ int mscd_get_memberships(mscd_ctx *c, int32_t scale_idx, int64_t *ptr, int32_t *
         if (nodes_cap < total || (total > 0 && !nodes)) { rc = MSCD_ESMALL; break; }
         if (total > 0) {
             if ((rc = cuda_status(cudaMallocAsync((void **)&dnodes, total * sizeof(i32), st)))) break;
-            gather_lists<<<152 * 8, 256, 0, st>>>(c->uoff + base, c->ulen + base, dptr, c->out_nodes, N, dnodes); note_launch();
+            gather_lists<<<152 * 8, 256, 0, st>>>(c->uoff + base, c->ulen + base, dptr,
+                                                  c->scales[scale_idx].comm_nodes, N, dnodes); note_launch();
             if ((rc = cuda_status(cudaMemcpyAsync(nodes, dnodes, total * sizeof(i32), cudaMemcpyDeviceToHost, st))))
                 break;
         }
@@ -768,13 +989,19 @@ int mscd_get_communities(mscd_ctx *c, int32_t scale_idx, int64_t *ptr, int64_t p
     return MSCD_OK;
 }
 
-int mscd_get_stability(mscd_ctx *c, double *nmi_succ, double *nmi_win3, double *nmi_win5) {
+int mscd_get_stability_part(mscd_ctx *c, int32_t part, double *nmi_succ, double *nmi_win3, double *nmi_win5) {
     if (!c) return MSCD_EINVAL;
     if (!c->have) return MSCD_ENORESULT;
-    if (nmi_succ) std::copy(c->nmi_succ.begin(), c->nmi_succ.end(), nmi_succ);
-    if (nmi_win3) std::copy(c->win3.begin(), c->win3.end(), nmi_win3);
-    if (nmi_win5) std::copy(c->win5.begin(), c->win5.end(), nmi_win5);
+    if (part < 0 || part >= c->n_parts) return MSCD_EINVAL;
+    const size_t S = (size_t)c->S, S1 = S ? S - 1 : 0;
+    if (nmi_succ) std::copy_n(c->nmi_succ.begin() + part * S1, S1, nmi_succ);
+    if (nmi_win3) std::copy_n(c->win3.begin() + part * S, S, nmi_win3);
+    if (nmi_win5) std::copy_n(c->win5.begin() + part * S, S, nmi_win5);
     return MSCD_OK;
+}
+
+int mscd_get_stability(mscd_ctx *c, double *nmi_succ, double *nmi_win3, double *nmi_win5) {
+    return mscd_get_stability_part(c, 0, nmi_succ, nmi_win3, nmi_win5);
 }
 
 int mscd_get_run_stats(mscd_ctx *c, mscd_run_stats *out) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <vector>
 #include <stdint.h>
 
 #include "mscd.h"
@@ -52,3 +53,9 @@ bool ctx_graph(mscd_ctx *c, int32_t graph_id, DevGraph *g, int *device);
 // Graph preparation (checks, exact weights, degrees, log degrees).
 int graph_prepare(i64 n, const i64 *rp_dev, const i32 *col_dev, const float *w_dev, DevGraph *g, i64 **wfx_out,
                   i64 **k_out, float **logk_out, cudaStream_t st);
+
+// Disjoint union of graphs as one graph (node ids of part p shifted by the
+// nodes of the parts before it); node_off gets the n_parts+1 offsets.  All parts
+// weighted or none; MSCD_ERANGE when the total exceeds the ranges of a load.
+int graph_union(const std::vector<DevGraph> &parts, DevGraph *out, i64 **rp_out, i32 **col_out, i64 **wfx_out,
+                i64 **k_out, float **logk_out, std::vector<i64> *node_off, cudaStream_t st);

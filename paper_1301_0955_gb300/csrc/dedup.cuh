@@ -19,4 +19,8 @@ int dedup_scale(const i64 *uoff, const i32 *ulen, const u64 *uhash, const double
                 ScaleResult *out, cudaStream_t st);
 
 // Overlapping NMI between two deduplicated community sets over n nodes.
-int nmi_between(const ScaleResult &X, const ScaleResult &Y, i64 n, double *nmi, cudaStream_t st);
+// nmi[p] for each part p of a graph that is a disjoint union (part_off:
+// device int64[n_parts+1] node offsets), or nmi[0] for the whole graph of n
+// nodes when part_off is null.  NaN where a side has no community.
+int nmi_between(const ScaleResult &X, const ScaleResult &Y, i64 n, const i64 *part_off, int32_t n_parts, double *nmi,
+                cudaStream_t st);

@@ -706,18 +706,20 @@ __global__ void __launch_bounds__(MAXT, MINB) grow_kernel(GrowArgs a) {
     const State<VT, HT, WEIGHTED> st = carve<VT, HT, WEIGHTED>(base, a.cap, bounds);
     for (int i = lane; i < st.H; i += 32) st.hsh[i] = 0;
     __syncwarp();
-    if (a.plain) {
-        const i64 t = a.work_base + gw;
-        if (t < a.n_work) grow_unit(st, a, a.work_list ? a.work_list[t] : a.unit_base + t);
-        return;
-    }
+    // one call site of grow_unit, and nothing of the plain form live across it
+    // (a second inlined copy, or a flag, costs registers)
     for (;;) {
         unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(a.work_counter, 1ull);
-        t = __shfl_sync(FULL_MASK, t, 0);
+        if (a.plain) {
+            t = (unsigned long long)(a.work_base + (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+        } else {
+            if (lane == 0) t = atomicAdd(a.work_counter, 1ull);
+            t = __shfl_sync(FULL_MASK, t, 0);
+        }
         if ((i64)t >= a.n_work) break;
         const i64 unit = a.work_list ? a.work_list[t] : a.unit_base + (i64)t;
         grow_unit(st, a, unit);
+        if (a.plain) break;
     }
 }
 

@@ -27,8 +27,15 @@
 // shared-memory hash; a community that meets too many partners is redone by
 // a whole CTA with a larger shared-memory table, and beyond that with a
 // global-memory table of its own.  Minima are kept as the bits of
-// non-negative doubles; per-community terms are summed in a fixed order, so
-// the value is deterministic.
+// non-negative doubles; the per-community terms are summed exactly (each
+// rounded once to a multiple of 2^-62, added in 128-bit integers), so the
+// value does not depend on the order of the additions.
+//
+// A graph that is a disjoint union of parts (independent graphs batched as
+// one) gets one NMI per part: a community lies inside one part (growth never
+// leaves the seed's component), n above is its part's node count, partners
+// are only ever taken from the same part, and the means run over each part's
+// communities.
 #include <algorithm>
 #include <vector>
 
@@ -132,16 +139,37 @@ __global__ void match_identical(const i64 *xptr, const i32 *xnodes, const u64 *x
     }
 }
 
+// Part of every community (that of its first member; a community never spans
+// parts) and that part's node count.  No offsets: one part of n nodes.
+__global__ void comm_parts(const i64 *ptr, const i32 *nodes, i64 C, const i64 *off, i32 n_parts, i64 n, i32 *cp,
+                           i64 *cn) {
+    for (i64 l = (i64)blockIdx.x * blockDim.x + threadIdx.x; l < C; l += (i64)gridDim.x * blockDim.x) {
+        if (!off) {
+            cp[l] = 0;
+            cn[l] = n;
+            continue;
+        }
+        const i64 u = nodes[ptr[l]];
+        i32 lo = 0, hi = n_parts - 1;  // last part with off[p] <= u
+        while (lo < hi) {
+            const i32 mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        cp[l] = lo;
+        cn[l] = off[lo + 1] - off[lo];
+    }
+}
+
 // Initial minima: 0 for communities with an identical partner, else H(C)
 // (the value when no partner is admitted); list the others.
-__global__ void init_best(const i64 *ptr, i64 C, i64 n, const unsigned char *zero, unsigned long long *best,
+__global__ void init_best(const i64 *ptr, i64 C, const i64 *cn, const unsigned char *zero, unsigned long long *best,
                           i32 *active, unsigned long long *n_active) {
-    const double inv_n = 1.0 / (double)n;
     for (i64 l = (i64)blockIdx.x * blockDim.x + threadIdx.x; l < C; l += (i64)gridDim.x * blockDim.x) {
         if (zero[l]) {
             best[l] = 0ull;
         } else {
-            best[l] = min_bits(entropy(ptr[l + 1] - ptr[l], n, inv_n));
+            best[l] = min_bits(entropy(ptr[l + 1] - ptr[l], cn[l], 1.0 / (double)cn[l]));
             active[atomicAdd(n_active, 1ull)] = (i32)l;
         }
     }
@@ -157,7 +185,7 @@ struct DirArgs {
     const i64 *bptr;
     const i64 *mptr;    // node -> communities of B
     const i32 *mlist;
-    i64 n;
+    const i64 *acn;            // per A community: node count of its part
     unsigned long long *best;  // per A community (bits of doubles)
     i64 *spill;                // positions in `active` redone with global tables
     unsigned long long *n_spill;
@@ -173,7 +201,6 @@ __global__ void __launch_bounds__(NMI_WARPS * 32) pairs_smem(DirArgs a) {
     __shared__ int sfill[NMI_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const i64 warps = (i64)gridDim.x * NMI_WARPS;
-    const double inv_n = 1.0 / (double)a.n;
     i32 *keys = skey[w];
     i32 *cnts = scnt[w];
     for (i64 q = (i64)blockIdx.x * NMI_WARPS + w; q < a.n_active; q += warps) {
@@ -214,11 +241,12 @@ __global__ void __launch_bounds__(NMI_WARPS * 32) pairs_smem(DirArgs a) {
             continue;
         }
         __syncwarp();
-        const i64 sa = a.aptr[k + 1] - a.aptr[k];
+        const i64 sa = a.aptr[k + 1] - a.aptr[k], n = a.acn[k];
+        const double inv_n = 1.0 / (double)n;
         double bx = __longlong_as_double((long long)a.best[k]);
         for (int t = lane; t < NMI_TABLE; t += 32) {
             const i32 l = keys[t];
-            if (l >= 0) bx = min(bx, cond_candidate(cnts[t], sa, a.bptr[l + 1] - a.bptr[l], a.n, inv_n));
+            if (l >= 0) bx = min(bx, cond_candidate(cnts[t], sa, a.bptr[l + 1] - a.bptr[l], n, inv_n));
         }
         for (int o = 16; o; o >>= 1) bx = min(bx, __shfl_xor_sync(FULL_MASK, bx, o));
         if (lane == 0) a.best[k] = min_bits(bx);
@@ -231,7 +259,6 @@ __global__ void __launch_bounds__(NMI_WARPS * 32) pairs_smem(DirArgs a) {
 __global__ void pairs_global(DirArgs a, const i64 *list, i64 nk) {
     const int lane = threadIdx.x & 31;
     const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
-    const double inv_n = 1.0 / (double)a.n;
     for (i64 r = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nk; r += warps) {
         const i32 k = a.active[list[r]];
         i32 *keys = a.tkey + a.toff[r];
@@ -257,11 +284,12 @@ __global__ void pairs_global(DirArgs a, const i64 *list, i64 nk) {
             }
         }
         __syncwarp();
-        const i64 sa = a.aptr[k + 1] - a.aptr[k];
+        const i64 sa = a.aptr[k + 1] - a.aptr[k], n = a.acn[k];
+        const double inv_n = 1.0 / (double)n;
         double bx = __longlong_as_double((long long)a.best[k]);
         for (u32 t = lane; t <= tm; t += 32) {
             const i32 l = keys[t];
-            if (l >= 0) bx = min(bx, cond_candidate(cnts[t], sa, a.bptr[l + 1] - a.bptr[l], a.n, inv_n));
+            if (l >= 0) bx = min(bx, cond_candidate(cnts[t], sa, a.bptr[l + 1] - a.bptr[l], n, inv_n));
         }
         for (int o = 16; o; o >>= 1) bx = min(bx, __shfl_xor_sync(FULL_MASK, bx, o));
         if (lane == 0) a.best[k] = min_bits(bx);
@@ -281,7 +309,6 @@ __global__ void __launch_bounds__(BLK_WARPS * 32) pairs_block(DirArgs a, const i
     __shared__ int fill, over;
     __shared__ double wmin[BLK_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const double inv_n = 1.0 / (double)a.n;
     for (i64 r = blockIdx.x; r < nk; r += gridDim.x) {
         const i64 q = list[r];
         const i32 k = a.active[q];
@@ -323,11 +350,12 @@ __global__ void __launch_bounds__(BLK_WARPS * 32) pairs_block(DirArgs a, const i
             __syncthreads();
             continue;
         }
-        const i64 sa = a.aptr[k + 1] - a.aptr[k];
+        const i64 sa = a.aptr[k + 1] - a.aptr[k], n = a.acn[k];
+        const double inv_n = 1.0 / (double)n;
         double bx = __builtin_huge_val();
         for (int t = threadIdx.x; t < BLK_TABLE; t += BLK_WARPS * 32) {
             const i32 l = keys[t];
-            if (l >= 0) bx = min(bx, cond_candidate(cnts[t], sa, a.bptr[l + 1] - a.bptr[l], a.n, inv_n));
+            if (l >= 0) bx = min(bx, cond_candidate(cnts[t], sa, a.bptr[l + 1] - a.bptr[l], n, inv_n));
         }
         for (int o = 16; o; o >>= 1) bx = min(bx, __shfl_xor_sync(FULL_MASK, bx, o));
         if (lane == 0) wmin[w] = bx;
@@ -360,16 +388,16 @@ __global__ void spill_sizes(const i64 *list, i64 nk, const i32 *active, const i6
 }
 
 // Disjoint pairs that can be admitted (|A| + |B| > n/2): every active A
-// against the listed large communities B; the pair is disjoint unless a merge
-// of the two sorted lists meets a common node.
+// against the listed large communities B of its part; the pair is disjoint
+// unless a merge of the two sorted lists meets a common node.
 __global__ void disjoint_pairs(const i64 *aptr, const i32 *anodes, const i32 *active, i64 n_active,
-                               const i64 *bptr, const i32 *bnodes, const i32 *big, i64 nbig, i64 n,
-                               unsigned long long *best) {
-    const double inv_n = 1.0 / (double)n;
+                               const i64 *bptr, const i32 *bnodes, const i32 *big, i64 nbig, const i32 *acp,
+                               const i64 *acn, const i32 *bcp, unsigned long long *best) {
     for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < n_active * nbig; t += (i64)gridDim.x * blockDim.x) {
         const i32 k = active[t / nbig];
         const i32 l = big[t % nbig];
-        const i64 sa = aptr[k + 1] - aptr[k], sb = bptr[l + 1] - bptr[l];
+        if (acp[k] != bcp[l]) continue;
+        const i64 sa = aptr[k + 1] - aptr[k], sb = bptr[l + 1] - bptr[l], n = acn[k];
         if (2 * (sa + sb) <= n) continue;
         const i32 *x = anodes + aptr[k], *y = bnodes + bptr[l];
         i64 i = 0, j = 0;
@@ -383,38 +411,34 @@ __global__ void disjoint_pairs(const i64 *aptr, const i32 *anodes, const i32 *ac
             }
         }
         if (meet) continue;
-        const double c = cond_candidate(0, sa, sb, n, inv_n);
+        const double c = cond_candidate(0, sa, sb, n, 1.0 / (double)n);
         if (c < __builtin_huge_val()) atomicMin(&best[k], min_bits(c));
     }
 }
 
-// Communities with 2(|B| + 1) > n: the only ones that can satisfy the
-// disjoint admission condition with a community of size >= 1.
-__global__ void list_big(const i64 *ptr, i64 C, i64 n, i32 *big, unsigned long long *nbig) {
+// Communities with 2(|B| + 1) > n (n of B's part): the only ones that can
+// satisfy the disjoint admission condition with a community of size >= 1.
+__global__ void list_big(const i64 *ptr, i64 C, const i64 *cn, i32 *big, unsigned long long *nbig) {
     for (i64 l = (i64)blockIdx.x * blockDim.x + threadIdx.x; l < C; l += (i64)gridDim.x * blockDim.x)
-        if (2 * (ptr[l + 1] - ptr[l] + 1) > n) big[atomicAdd(nbig, 1ull)] = (i32)l;
+        if (2 * (ptr[l + 1] - ptr[l] + 1) > cn[l]) big[atomicAdd(nbig, 1ull)] = (i32)l;
 }
 
-__global__ void normalise(const i64 *ptr, i64 C, i64 n, const unsigned long long *best, double *term) {
-    const double inv_n = 1.0 / (double)n;
+// Normalised term H(A_k|B) / H(A_k) in [0, 1] (the minimum never exceeds its
+// initial value H(A_k), computed the same way), added to its part's total as
+// an integer multiple of 2^-62 in 128 bits: acc[2p] low word, acc[2p+1] carries.
+__global__ void normalise_sum(const i64 *ptr, i64 C, const i64 *cn, const i32 *cp,
+                              const unsigned long long *best, unsigned long long *acc,
+                              unsigned long long *count) {
     for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < C; k += (i64)gridDim.x * blockDim.x) {
-        const double H = entropy(ptr[k + 1] - ptr[k], n, inv_n);
-        term[k] = H > 0.0 ? __longlong_as_double((long long)best[k]) / H : 0.0;
+        const i64 n = cn[k];
+        const double H = entropy(ptr[k + 1] - ptr[k], n, 1.0 / (double)n);
+        const double t = H > 0.0 ? __longlong_as_double((long long)best[k]) / H : 0.0;
+        const unsigned long long q = (unsigned long long)__double2ll_rn(fmin(fmax(t, 0.0), 1.0) * 0x1p62);
+        const i32 p = cp[k];
+        const unsigned long long old = atomicAdd(&acc[2 * p], q);
+        if (old + q < old) atomicAdd(&acc[2 * p + 1], 1ull);
+        atomicAdd(&count[p], 1ull);
     }
-}
-
-// Fixed-order sum of term[0..m) by one block.
-__global__ void sum_fixed(const double *term, i64 m, double *out) {
-    __shared__ double part[1024];
-    double s = 0.0;
-    for (i64 i = threadIdx.x; i < m; i += blockDim.x) s += term[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = part[0];
 }
 
 template <class T>
@@ -459,8 +483,14 @@ void free_memberships(Memberships *M, cudaStream_t st) {
 }
 
 // Minimum admitted H(A_k|B) for every active A_k into best[] (one direction).
-int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships &MB, i64 n, const i32 *active,
-                  i64 n_active, unsigned long long *best, cudaStream_t st) {
+// Per-community part data of one scale's communities.
+struct CommParts {
+    i32 *cp = nullptr;  // part index
+    i64 *cn = nullptr;  // node count of that part
+};
+
+int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships &MB, const CommParts &PA,
+                  const CommParts &PB, const i32 *active, i64 n_active, unsigned long long *best, cudaStream_t st) {
     i64 *spill = nullptr, *spill2 = nullptr, *tsz = nullptr, *toff = nullptr;
     i32 *tkey = nullptr, *tcnt = nullptr, *big = nullptr;
     unsigned long long *cnt = nullptr;
@@ -479,13 +509,13 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
         a.bptr = B.comm_ptr;
         a.mptr = MB.ptr;
         a.mlist = MB.list;
-        a.n = n;
+        a.acn = PA.cn;
         a.best = best;
         a.spill = spill;
         a.n_spill = cnt;
         pairs_smem<<<(unsigned)std::min<i64>((n_active + NMI_WARPS - 1) / NMI_WARPS, 152 * 3), NMI_WARPS * 32, 0,
                      st>>>(a); note_launch();
-        list_big<<<GB, 256, 0, st>>>(B.comm_ptr, B.n_comms, n, big, cnt + 1); note_launch();
+        list_big<<<GB, 256, 0, st>>>(B.comm_ptr, B.n_comms, PB.cn, big, cnt + 1); note_launch();
         unsigned long long h[2] = {0, 0};
         if ((rc = cuda_status(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st)))) break;
         if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
@@ -524,7 +554,7 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
         }
         if (h[1] > 0) {
             disjoint_pairs<<<GB, 256, 0, st>>>(A.comm_ptr, A.comm_nodes, active, n_active, B.comm_ptr, B.comm_nodes,
-                                               big, (i64)h[1], n, best); note_launch();
+                                               big, (i64)h[1], PA.cp, PA.cn, PB.cp, best); note_launch();
         }
     } while (0);
     cudaFreeAsync(spill, st);
@@ -540,21 +570,23 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
 
 }  // namespace
 
-int nmi_between(const ScaleResult &X, const ScaleResult &Y, i64 n, double *nmi, cudaStream_t st) {
+int nmi_between(const ScaleResult &X, const ScaleResult &Y, i64 n, const i64 *part_off, int32_t n_parts, double *nmi,
+                cudaStream_t st) {
     const i64 CX = X.n_comms, CY = Y.n_comms;
-    if (CX <= 0 || CY <= 0 || n <= 0) {
-        *nmi = __builtin_nan("");
-        return MSCD_OK;
-    }
+    const int32_t P = part_off ? n_parts : 1;
+    for (int32_t p = 0; p < P; ++p) nmi[p] = __builtin_nan("");
+    if (CX <= 0 || CY <= 0 || n <= 0) return MSCD_OK;
     u64 *tkey = nullptr;
     i32 *tval = nullptr, *actX = nullptr, *actY = nullptr;
     unsigned char *zeroX = nullptr, *zeroY = nullptr;
-    unsigned long long *bestX = nullptr, *bestY = nullptr, *cnt = nullptr;
-    double *termX = nullptr, *termY = nullptr, *sums = nullptr;
+    unsigned long long *bestX = nullptr, *bestY = nullptr, *cnt = nullptr, *acc = nullptr;
+    CommParts PX, PY;
     Memberships MX, MY;
     int rc = MSCD_OK;
     i64 T = 2;
     while (T < 2 * CY) T <<= 1;
+    // acc: per part, X's 128-bit sum, Y's 128-bit sum, X's count, Y's count
+    const i64 acc_words = 6 * (i64)P;
     do {
         if ((rc = dev_alloc(&tkey, T, st))) break;
         if ((rc = dev_alloc(&tval, T, st))) break;
@@ -564,41 +596,53 @@ int nmi_between(const ScaleResult &X, const ScaleResult &Y, i64 n, double *nmi, 
         if ((rc = dev_alloc(&bestY, CY, st))) break;
         if ((rc = dev_alloc(&actX, CX, st))) break;
         if ((rc = dev_alloc(&actY, CY, st))) break;
+        if ((rc = dev_alloc(&PX.cp, CX, st))) break;
+        if ((rc = dev_alloc(&PX.cn, CX, st))) break;
+        if ((rc = dev_alloc(&PY.cp, CY, st))) break;
+        if ((rc = dev_alloc(&PY.cn, CY, st))) break;
         if ((rc = dev_alloc(&cnt, 2, st))) break;
-        if ((rc = dev_alloc(&termX, CX, st))) break;
-        if ((rc = dev_alloc(&termY, CY, st))) break;
-        if ((rc = dev_alloc(&sums, 2, st))) break;
+        if ((rc = dev_alloc(&acc, acc_words, st))) break;
         if ((rc = cuda_status(cudaMemsetAsync(tkey, 0, T * sizeof(u64), st)))) break;
         if ((rc = cuda_status(cudaMemsetAsync(zeroX, 0, CX, st)))) break;
         if ((rc = cuda_status(cudaMemsetAsync(zeroY, 0, CY, st)))) break;
         if ((rc = cuda_status(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st)))) break;
+        if ((rc = cuda_status(cudaMemsetAsync(acc, 0, acc_words * sizeof(unsigned long long), st)))) break;
+        comm_parts<<<GB, 256, 0, st>>>(X.comm_ptr, X.comm_nodes, CX, part_off, P, n, PX.cp, PX.cn); note_launch();
+        comm_parts<<<GB, 256, 0, st>>>(Y.comm_ptr, Y.comm_nodes, CY, part_off, P, n, PY.cp, PY.cn); note_launch();
         // identical communities
         hash_insert<<<GB, 256, 0, st>>>(Y.comm_hash, CY, tkey, tval, T - 1); note_launch();
         match_identical<<<GB, 256, 0, st>>>(X.comm_ptr, X.comm_nodes, X.comm_hash, CX, Y.comm_ptr, Y.comm_nodes, tkey,
                                             tval, T - 1, zeroX, zeroY); note_launch();
-        init_best<<<GB, 256, 0, st>>>(X.comm_ptr, CX, n, zeroX, bestX, actX, cnt); note_launch();
-        init_best<<<GB, 256, 0, st>>>(Y.comm_ptr, CY, n, zeroY, bestY, actY, cnt + 1); note_launch();
+        init_best<<<GB, 256, 0, st>>>(X.comm_ptr, CX, PX.cn, zeroX, bestX, actX, cnt); note_launch();
+        init_best<<<GB, 256, 0, st>>>(Y.comm_ptr, CY, PY.cn, zeroY, bestY, actY, cnt + 1); note_launch();
         unsigned long long na[2] = {0, 0};
         if ((rc = cuda_status(cudaMemcpyAsync(na, cnt, sizeof(na), cudaMemcpyDeviceToHost, st)))) break;
         if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
         // H(X_k|Y) for the X communities without an identical partner
         if (na[0] > 0) {
             if ((rc = build_memberships(Y, n, &MY, st))) break;
-            if ((rc = one_direction(X, Y, MY, n, actX, (i64)na[0], bestX, st))) break;
+            if ((rc = one_direction(X, Y, MY, PX, PY, actX, (i64)na[0], bestX, st))) break;
         }
         // H(Y_l|X) likewise
         if (na[1] > 0) {
             if ((rc = build_memberships(X, n, &MX, st))) break;
-            if ((rc = one_direction(Y, X, MX, n, actY, (i64)na[1], bestY, st))) break;
+            if ((rc = one_direction(Y, X, MX, PY, PX, actY, (i64)na[1], bestY, st))) break;
         }
-        normalise<<<GB, 256, 0, st>>>(X.comm_ptr, CX, n, bestX, termX); note_launch();
-        normalise<<<GB, 256, 0, st>>>(Y.comm_ptr, CY, n, bestY, termY); note_launch();
-        sum_fixed<<<1, 1024, 0, st>>>(termX, CX, sums); note_launch();
-        sum_fixed<<<1, 1024, 0, st>>>(termY, CY, sums + 1); note_launch();
-        double hs[2] = {0.0, 0.0};
-        if ((rc = cuda_status(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st)))) break;
+        normalise_sum<<<GB, 256, 0, st>>>(X.comm_ptr, CX, PX.cn, PX.cp, bestX, acc, acc + 4 * P); note_launch();
+        normalise_sum<<<GB, 256, 0, st>>>(Y.comm_ptr, CY, PY.cn, PY.cp, bestY, acc + 2 * P, acc + 5 * P);
+        note_launch();
+        std::vector<unsigned long long> h(acc_words);
+        if ((rc = cuda_status(cudaMemcpyAsync(h.data(), acc, acc_words * sizeof(unsigned long long),
+                                              cudaMemcpyDeviceToHost, st))))
+            break;
         if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
-        *nmi = 1.0 - 0.5 * (hs[0] / (double)CX + hs[1] / (double)CY);
+        for (int32_t p = 0; p < P; ++p) {
+            const unsigned long long cx = h[4 * P + p], cy = h[5 * P + p];
+            if (!cx || !cy) continue;  // a part without communities at one of the scales
+            const double sx = (double)h[2 * p + 1] * 4.0 + (double)h[2 * p] * 0x1p-62;
+            const double sy = (double)h[2 * P + 2 * p + 1] * 4.0 + (double)h[2 * P + 2 * p] * 0x1p-62;
+            nmi[p] = 1.0 - 0.5 * (sx / (double)cx + sy / (double)cy);
+        }
     } while (0);
     free_memberships(&MX, st);
     free_memberships(&MY, st);
@@ -610,9 +654,11 @@ int nmi_between(const ScaleResult &X, const ScaleResult &Y, i64 n, double *nmi, 
     cudaFreeAsync(bestY, st);
     cudaFreeAsync(actX, st);
     cudaFreeAsync(actY, st);
+    cudaFreeAsync(PX.cp, st);
+    cudaFreeAsync(PX.cn, st);
+    cudaFreeAsync(PY.cp, st);
+    cudaFreeAsync(PY.cn, st);
     cudaFreeAsync(cnt, st);
-    cudaFreeAsync(termX, st);
-    cudaFreeAsync(termY, st);
-    cudaFreeAsync(sums, st);
+    cudaFreeAsync(acc, st);
     return rc != MSCD_OK ? rc : cuda_status(cudaGetLastError());
 }

@@ -21,6 +21,8 @@ ETIMEOUT, ESMALL, EUNDECIDED, EUNSORTED, EWEIGHT, ENORESULT = -8, -9, -10, -11, 
 DEVICE_PTRS = 1
 SCHED_PERSISTENT = 0
 SCHED_PER_SCALE = 1
+TUNE_APPLY = 1
+TUNE_CACHED = 2
 NSTATS = 8
 STAT_FIELDS = ("edges_scanned", "adds", "removes", "rounds", "K", "V", "slow", "undecided")
 
@@ -71,6 +73,10 @@ SIGNATURES = {
     "mscd_get_memberships": (C.c_int, [vp, C.c_int32, i64p, i32p, C.c_int64, f64p, i64p, i64p]),
     "mscd_get_communities": (C.c_int, [vp, C.c_int32, i64p, C.c_int64, i32p, C.c_int64, f64p, i32p, i64p, i64p]),
     "mscd_get_stability": (C.c_int, [vp, f64p, f64p, f64p]),
+    "mscd_get_stability_part": (C.c_int, [vp, C.c_int32, f64p, f64p, f64p]),
+    "mscd_autotune": (C.c_int, [vp, C.c_int32, f64p, C.c_int32, C.c_int64, C.c_uint32, C.POINTER(mscd_params), f64p]),
+    "mscd_graph_union": (C.c_int, [vp, i32p, C.c_int32, i32p]),
+    "mscd_graph_parts": (C.c_int, [vp, C.c_int32, i64p, C.c_int32, i32p]),
     "mscd_get_run_stats": (C.c_int, [vp, C.POINTER(mscd_run_stats)]),
     "mscd_grow_noalloc": (C.c_int, [vp, C.c_int32, f64p, C.c_int32, vp, C.c_int64, vp, C.c_int64, vp, vp, vp, vp,
                                     vp, vp, i64p, vp]),
@@ -175,6 +181,36 @@ class Context:
     def free_graph(self, gid: int):
         _check(load().mscd_graph_free(self.h, gid), "mscd_graph_free")
 
+    def autotune(self, gid: int, alphas, n_sample: int = 0, apply: bool = True, cached: bool = False):
+        """Pick the fastest slot classes and residency on a seeded sample (see
+        mscd_autotune); returns (params dict, growth ms on the sample)."""
+        alphas = np.ascontiguousarray(alphas, np.float64)
+        p = mscd_params()
+        ms = C.c_double()
+        flags = (TUNE_APPLY if apply else 0) | (TUNE_CACHED if cached else 0)
+        _check(load().mscd_autotune(self.h, gid, alphas.ctypes.data_as(f64p), len(alphas), n_sample, flags,
+                                    C.byref(p), C.byref(ms)), "mscd_autotune")
+        return {k: getattr(p, k) for k, _ in mscd_params._fields_}, ms.value
+
+    def graph_union(self, gids) -> int:
+        """Disjoint union of resident graphs as one resident graph (batching)."""
+        ids = np.ascontiguousarray(gids, np.int32)
+        out = C.c_int32(-1)
+        _check(load().mscd_graph_union(self.h, ids.ctypes.data_as(i32p), len(ids), C.byref(out)),
+               "mscd_graph_union")
+        return out.value
+
+    def graph_parts(self, gid: int) -> np.ndarray:
+        """Node offsets of the parts (int64[n_parts+1])."""
+        P = C.c_int32()
+        rc = load().mscd_graph_parts(self.h, gid, None, 0, C.byref(P))
+        if rc not in (OK, ESMALL):
+            _check(rc, "mscd_graph_parts")
+        off = np.zeros(P.value + 1, np.int64)
+        _check(load().mscd_graph_parts(self.h, gid, off.ctypes.data_as(i64p), len(off), C.byref(P)),
+               "mscd_graph_parts")
+        return off
+
     def graph_info(self, gid: int) -> dict:
         n, nnz, vol = C.c_int64(), C.c_int64(), C.c_int64()
         ue = C.c_int32()
@@ -253,13 +289,19 @@ class Context:
                "mscd_get_communities")
         return ptr, nodes[: nn.value], f[: nc.value], s2c[: self.n_seeds]
 
-    def stability(self):
+    def stability(self, part=None):
+        """(nmi_succ, window-3 means, window-5 means) of the last run, or of one
+        part of a union graph."""
         S = self.n_scales
         a = np.zeros(max(S - 1, 1), np.float64)
         b = np.zeros(S, np.float64)
         c = np.zeros(S, np.float64)
-        _check(load().mscd_get_stability(self.h, a.ctypes.data_as(f64p), b.ctypes.data_as(f64p),
-                                         c.ctypes.data_as(f64p)), "mscd_get_stability")
+        if part is None:
+            _check(load().mscd_get_stability(self.h, a.ctypes.data_as(f64p), b.ctypes.data_as(f64p),
+                                             c.ctypes.data_as(f64p)), "mscd_get_stability")
+        else:
+            _check(load().mscd_get_stability_part(self.h, part, a.ctypes.data_as(f64p), b.ctypes.data_as(f64p),
+                                                  c.ctypes.data_as(f64p)), "mscd_get_stability_part")
         return a[: S - 1], b, c
 
     def grow_noalloc(self, gid: int, alphas, seeds, out: dict, stream=None):

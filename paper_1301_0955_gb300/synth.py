@@ -225,16 +225,27 @@ def config_graph(idx: int) -> CSRGraph:
     raise ValueError(idx)
 
 
-def uneven_batch(n_graphs=256, seed=4, n_range=(1_000, 200_000), scale_nodes=1.0):
-    """Many independent two-level graphs of log-uniform size (batching workload)."""
+def uneven_batch_specs(n_graphs=256, seed=4, n_range=(1_000, 200_000), scale_nodes=1.0):
+    """Parameters of the graphs of the uneven batch: node counts log-uniform in
+    n_range (times scale_nodes), mean degree uniform in [10, 40], micro mixing
+    uniform in [0.2, 0.4] (macro a third of it), two levels."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    out = []
+    specs = []
     for i in range(n_graphs):
         n = int(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1]))) * scale_nodes)
         n = max(n, 100)
         md = float(rng.uniform(10, 40))
         mu = float(rng.uniform(0.2, 0.4))
-        out.append(hierarchical_lfr(n, md, max(4 * int(md), 40), 2.5, 1.5, (20, 1000), (mu, mu / 3),
-                                    seed=1000 + i, name=f"uneven-{i}"))
-    return out
+        specs.append(dict(n=n, mean_deg=md, max_deg=max(4 * int(md), 40), tau_deg=2.5, tau_size=1.5,
+                          size_range=(20, 1000), mixing=(mu, mu / 3), seed=1000 + i, name=f"uneven-{i}"))
+    return specs
+
+
+def graph_from_spec(spec):
+    return hierarchical_lfr(**spec)
+
+
+def uneven_batch(n_graphs=256, seed=4, n_range=(1_000, 200_000), scale_nodes=1.0):
+    """Many independent two-level graphs of log-uniform size (batching workload)."""
+    return [graph_from_spec(sp) for sp in uneven_batch_specs(n_graphs, seed, n_range, scale_nodes)]
 
