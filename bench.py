@@ -59,7 +59,13 @@ def parse_args():
     p.add_argument("--flush-mib", type=int, default=1024, help="L2 flush buffer written between steps")
     p.add_argument("--plain-steps", type=int, default=1,
                    help="steps of the plain one-launch-per-scale form timed for comparison (0: skip)")
-    p.add_argument("--workload", default="lfr-100k", choices=["lfr-100k", "uneven-batch"])
+    p.add_argument("--workload", default="lfr-100k", choices=["lfr-100k", "uneven-batch", "serve"])
+    p.add_argument("--serve-queries", type=int, default=10000, help="serve: queries per load level")
+    p.add_argument("--serve-calibration", type=int, default=1000, help="serve: queries of the saturation run")
+    p.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95])
+    p.add_argument("--serve-workers", type=int, default=4)
+    p.add_argument("--serve-batch-units", type=int, default=65536)
+    p.add_argument("--serve-node-scale", type=float, default=1.0, help="serve: node count factor")
     p.add_argument("--batch-graphs", type=int, default=256, help="uneven-batch: number of graphs")
     p.add_argument("--batch-node-scale", type=float, default=1.0, help="uneven-batch: node count factor")
     p.add_argument("--batch-scales", type=int, default=16, help="uneven-batch: scales")
@@ -353,6 +359,102 @@ class UnevenBatch:
 WORKLOADS = {"lfr-100k": Lfr100k, "uneven-batch": UnevenBatch}
 
 
+def percentile(xs, q):
+    return float(np.percentile(np.asarray(xs, np.float64), q)) if len(xs) else None
+
+
+def serve_phase(ctx, gids, alphas, queries, rate_qps):
+    """Offer `queries` (graph, scale index, seeds) at Poisson arrivals of
+    `rate_qps` (None: all at once), collect every result; returns latencies
+    (submit to done, ms), wall seconds and units."""
+    rng = np.random.default_rng(99)
+    n = len(queries)
+    arrivals = np.zeros(n) if rate_qps is None else np.cumsum(rng.exponential(1.0 / rate_qps, n))
+    out = {}
+    lat = []
+    queued = []
+    t0 = time.perf_counter()
+    i = 0
+    while len(lat) < n:
+        now = time.perf_counter() - t0
+        while i < n and arrivals[i] <= now:
+            g, s, seeds = queries[i]
+            out[ctx.submit(gids[g], seeds, alphas[s])] = len(seeds)
+            i += 1
+        done = [q for q in list(out) if ctx.poll(q) == 2]
+        for q in done:
+            ptr, nodes, f, t, rc = ctx.result(q, out.pop(q))
+            assert rc == 0, rc
+            lat.append(t[2])
+            queued.append(t[0])
+        if not done:
+            time.sleep(0.0002)
+    wall = time.perf_counter() - t0
+    units = sum(len(q[2]) for q in queries)
+    return {"latency_ms": lat, "queue_ms": queued, "wall_s": wall, "units": units}
+
+
+def run_serve(args):
+    """Serving: resident graphs, a Poisson stream of local-community queries,
+    continuous batching; p50/p99 latency at fractions of saturation."""
+    import multiprocessing as mp
+
+    from paper_1301_0955_gb300 import build, mscd, synth
+
+    world, rank, local = dist_env()
+    specs = synth.serving_specs(scale_nodes=args.serve_node_scale)
+    with mp.get_context("spawn").Pool(len(specs)) as pool:
+        graphs = pool.map(synth.graph_from_spec, specs, chunksize=1)
+    sizes = [g.n for g in graphs]
+    alphas = None
+    import torch
+
+    torch.cuda.set_device(local)
+    build.build()
+    L = mscd.load()
+    alphas = mscd.scales_logspaced(0.5, 1.0, 16)
+    ctx = mscd.Context(local)
+    gids = [ctx.load_csr(g.n, g.row_ptr, g.col) for g in graphs]
+    ctx.serve_start(workers=args.serve_workers, max_batch_units=args.serve_batch_units)
+    try:
+        # warm-up, then saturation: everything offered at once
+        serve_phase(ctx, gids, alphas, synth.serving_queries(50, sizes, seed=6), None)
+        sat_q = synth.serving_queries(args.serve_calibration, sizes, seed=8)
+        l0 = L.mscd_launch_count()
+        sat = serve_phase(ctx, gids, alphas, sat_q, None)
+        sat_qps = len(sat_q) / sat["wall_s"]
+        rows = []
+        queries = synth.serving_queries(args.serve_queries, sizes, seed=7)
+        for frac in args.serve_loads:
+            rate = frac * sat_qps
+            with ClockSampler(local) as clk:
+                r = serve_phase(ctx, gids, alphas, queries, rate)
+            rows.append({"load": frac, "offered_qps": rate, "achieved_qps": len(queries) / r["wall_s"],
+                         "units_per_s": r["units"] / r["wall_s"], "p50_ms": percentile(r["latency_ms"], 50),
+                         "p99_ms": percentile(r["latency_ms"], 99), "mean_ms": float(np.mean(r["latency_ms"])),
+                         "queue_p50_ms": percentile(r["queue_ms"], 50), "queue_p99_ms": percentile(r["queue_ms"], 99),
+                         "queries": len(queries), "clocks": clk.summary()})
+        st = ctx.serve_stats()
+        launches = L.mscd_launch_count() - l0
+    finally:
+        ctx.serve_stop()
+    mid = rows[len(rows) // 2] if rows else None
+    line = {"metric": "served local-community queries: p50/p99 latency and throughput",
+            "value": mid["p99_ms"] if mid else None, "unit": "ms (p99 at %g of saturation)" % (mid["load"] if mid else 0),
+            "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "int64+f64",
+            "config": {"workload": "serving: %d resident LFR-style graphs of %d nodes (mean degree 25, max 250, three "
+                                   "levels, mixing 0.3/0.2/0.1, unweighted); Poisson queries, each on a uniform "
+                                   "graph with 1-4096 uniform seeds at one of 16 log-spaced scales in [0.5,1]"
+                                   % (len(graphs), sizes[0]),
+                       "nnz": [g.nnz for g in graphs], "workers": args.serve_workers,
+                       "max_batch_units": args.serve_batch_units},
+            "saturation": {"queries": len(sat_q), "qps": sat_qps, "units_per_s": sat["units"] / sat["wall_s"],
+                           "p50_ms": percentile(sat["latency_ms"], 50), "p99_ms": percentile(sat["latency_ms"], 99)},
+            "loads": rows, "server_stats": st, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def read_results(ctx, n_scales, n_parts):
     """Device->host read of every scale's communities and every part's
     stability; returns the bytes read."""
@@ -366,13 +468,61 @@ def read_results(ctx, n_scales, n_parts):
     return nb
 
 
+class ServeSample:
+    """Reference arm of the serving workload: the oracle answers queries of the
+    same stream one after another (growth from every seed of the query)."""
+
+    name = "serve"
+
+    def __init__(self, args):
+        import multiprocessing as mp
+
+        from paper_1301_0955_gb300 import synth
+
+        specs = synth.serving_specs(scale_nodes=args.serve_node_scale)
+        with mp.get_context("spawn").Pool(len(specs)) as pool:
+            self.graphs = pool.map(synth.graph_from_spec, specs, chunksize=1)
+        import oracle
+
+        rc, self.alphas = oracle.scales_logspaced(0.5, 1.0, 16)
+        self.queries = synth.serving_queries(args.serve_queries, [g.n for g in self.graphs], seed=7)
+
+    def config(self):
+        return {"workload": "serving: %d resident LFR-style graphs of %d nodes, Poisson queries with 1-4096 seeds "
+                            "at one of 16 scales (the oracle answers a prefix of the stream in turn)"
+                            % (len(self.graphs), self.graphs[0].n)}
+
+    def cpu_baseline(self, seconds, threads):
+        import oracle
+
+        Gs = [oracle.Graph(g.n, g.row_ptr, g.col) for g in self.graphs]
+        units = 0
+        dt = 0.0
+        k = 0
+        lat = []
+        for g, s, seeds in self.queries:
+            t0 = time.perf_counter()
+            oracle.run(Gs[g], np.array([self.alphas[s]]), seeds, threads=threads)
+            t = time.perf_counter() - t0
+            lat.append(t * 1e3)
+            dt += t
+            units += len(seeds)
+            k += 1
+            if dt >= seconds:
+                break
+        return {"value": units / dt, "unit": "units/s", "cores": threads, "kind": "oracle",
+                "sample": "the first %d queries of the stream (%d seeds), answered one after another by the "
+                          "oracle on %d host threads, %.1f s; median query %.0f ms" % (k, units, threads, dt,
+                                                                                     float(np.median(lat)))}
+
+
 def run_reference(args):
     world, rank, local = dist_env()
     if rank != 0:
         return
     import oracle
 
-    wl = WORKLOADS[args.workload](args)
+    wl = ServeSample(args) if args.workload == "serve" else WORKLOADS[args.workload](args)
     threads = os.cpu_count() or 1
     per_step = max(1.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
@@ -395,6 +545,9 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     world, rank, local = dist_env()
     wl = WORKLOADS[args.workload](args)  # host-side generation before the first GPU call

@@ -54,6 +54,8 @@ extern "C" {
 #define MSCD_EUNSORTED (-11)  /* a CSR row is not in ascending column order       */
 #define MSCD_EWEIGHT (-12)    /* a weight that is not finite and > 0              */
 #define MSCD_ENORESULT (-13)  /* no successful run to read results from           */
+#define MSCD_EBUSY (-14)      /* in use: a graph queries still need, or a server
+                                 already running                                 */
 
 /* ---- flags ------------------------------------------------------------- */
 #define MSCD_DEVICE_PTRS 1u   /* array arguments are device pointers             */
@@ -204,6 +206,19 @@ int mscd_scales_logspaced(double vmin, double a, int32_t x, double *out);
 int mscd_run(mscd_ctx *ctx, int32_t graph_id, const double *alphas, int32_t n_scales, const int32_t *seeds,
              int64_t n_seeds, uint32_t flags, void *cuda_stream);
 
+/* The same, each community starting from its seed plus given initial members
+ * (Alg. 2: "a set of initial communities is given in input"): init_ptr
+ * int64[n_seeds+1] (init_ptr[0] = 0, non-decreasing) and init_nodes
+ * int32[init_ptr[n_seeds]] list the members for seed i at
+ * init_ptr[i]..init_ptr[i+1] (any order; repeats and the seed are ignored).
+ * The members join before the first grow pass (not counted as additions);
+ * the seed stays pinned; a community that no addition improves is returned
+ * as given (prune passes follow additions only, Alg. 1).  seeds must not be
+ * NULL.  Host or device pointers as flags say. */
+int mscd_run_init(mscd_ctx *ctx, int32_t graph_id, const double *alphas, int32_t n_scales, const int32_t *seeds,
+                  int64_t n_seeds, const int64_t *init_ptr, const int32_t *init_nodes, uint32_t flags,
+                  void *cuda_stream);
+
 /* Membership of one unit: the sorted member list (host int32, cap entries),
  * its length and its fitness f (Eq. 1 in the original weight units). */
 int mscd_get_membership(mscd_ctx *ctx, int32_t scale_idx, int64_t seed_idx, int32_t *buf, int64_t cap,
@@ -255,6 +270,11 @@ int mscd_get_stability_part(mscd_ctx *ctx, int32_t part, double *nmi_succ, doubl
 /* Totals of the last run. */
 int mscd_get_run_stats(mscd_ctx *ctx, mscd_run_stats *out);
 
+/* Where the last failed mscd_run stopped and why ("" if none failed), e.g.
+ * "mscd_run: dedup of scale 3: device memory allocation failed".  The string
+ * belongs to the context and stays valid until its next failed run. */
+const char *mscd_last_error(mscd_ctx *ctx);
+
 /* Growth of every (scale, seed) unit without allocating device memory during
  * the call.  The paper has no counterpart: this entry point exists for
  * callers that cannot call cudaMalloc while they run (a process with a fixed
@@ -285,6 +305,72 @@ int mscd_grow_noalloc(mscd_ctx *ctx, int32_t graph_id, const double *alphas, int
                       const int32_t *seeds, int64_t n_seeds, int32_t *out_nodes, int64_t out_cap,
                       int64_t *out_offset, int32_t *out_len, double *out_fitness, int64_t *out_stats,
                       int32_t *out_status, uint64_t *out_hash, int64_t *n_nodes_needed, void *cuda_stream);
+
+/* ------------------------------------------------------------------ serving
+ * Local-community queries answered as they arrive (no counterpart in the
+ * paper, whose method runs over all seeds at once; a query is the growth of
+ * Alg. 1 from each of its seeds at one scale, the unit a run computes).
+ *
+ * mscd_serve_start starts `workers` host threads, each with its own CUDA
+ * stream and growth buffers.  Waiting queries are batched continuously: a
+ * free worker takes the oldest waiting query and every later one on the same
+ * graph that fits its batch (max_batch_units seeds) and the memory budget,
+ * and grows them in one persistent launch (plus the larger slot classes);
+ * while it runs, other workers admit and launch the queries that arrive, so
+ * batches overlap on the device.  Admission by memory: a query holds, until
+ * its batch completes, its per-seed records plus its expected member lists
+ * (the mean length seen on its graph, with a margin); a batch waits while the
+ * holdings in flight would pass memory_budget (an oversized query runs alone).
+ * Every seed is grown independently and exactly: a query's result is the same
+ * alone and in any mix.  Graphs a waiting or running query uses cannot be
+ * freed (MSCD_EBUSY).  The server's calls are thread-safe among themselves. */
+typedef struct mscd_serve_params {
+    int32_t struct_size;      /* sizeof(mscd_serve_params)                        */
+    int32_t workers;          /* concurrent batches (0 = 4, at most 64)           */
+    int64_t max_batch_units;  /* seeds per batch and per query (0 = 65536)        */
+    int64_t memory_budget;    /* bytes batches in flight may hold (0 = a quarter
+                                 of the free device memory at start)              */
+} mscd_serve_params;
+
+typedef struct mscd_serve_stats {
+    int64_t queries_submitted, queries_done, units_done, batches;
+    int64_t queued;               /* waiting now                                  */
+    int64_t in_flight_bytes;      /* held by running batches now                  */
+    int64_t max_in_flight_bytes;  /* largest holding seen                         */
+    int64_t budget_bytes;
+} mscd_serve_stats;
+
+#define MSCD_Q_QUEUED 0
+#define MSCD_Q_RUNNING 1
+#define MSCD_Q_DONE 2
+
+/* Start (EBUSY if running) / stop (waits for every queued and running query;
+ * results not collected are dropped) the server of a context.  The node-slot
+ * parameters of the context apply to its batches (persistent schedule). */
+int mscd_serve_start(mscd_ctx *ctx, const mscd_serve_params *params);
+int mscd_serve_stop(mscd_ctx *ctx);
+
+/* Queue a query: seeds int32[n_seeds] (host, copied; 1 <= n_seeds <=
+ * max_batch_units, else ERANGE; ids in [0, n) of the graph, else EINVAL) on
+ * resident graph graph_id at scale alpha (finite, > 0).  *qid names it. */
+int mscd_query_submit(mscd_ctx *ctx, int32_t graph_id, const int32_t *seeds, int32_t n_seeds, double alpha,
+                      uint64_t *qid);
+
+/* State of a query (MSCD_Q_*); wait: until done or timeout_us passed. */
+int mscd_query_poll(mscd_ctx *ctx, uint64_t qid, int32_t *state);
+int mscd_query_wait(mscd_ctx *ctx, uint64_t qid, int64_t timeout_us, int32_t *state);
+
+/* Result of a done query (ENORESULT before): ptr int64[n_seeds+1] offsets of
+ * each seed's sorted member list in nodes int32[nodes_cap], fitness
+ * double[n_seeds] (may be NULL), *n_nodes the list entries; times_ms (may be
+ * NULL) double[3] = queued, running, submit-to-done milliseconds.  ESMALL
+ * (with *n_nodes) leaves the query in place; otherwise the query is released
+ * and its status returned (OK, ETIMEOUT, EUNDECIDED, or the error that failed
+ * its batch). */
+int mscd_query_result(mscd_ctx *ctx, uint64_t qid, int64_t *ptr, int32_t *nodes, int64_t nodes_cap,
+                      double *fitness, int64_t *n_nodes, double *times_ms);
+
+int mscd_serve_get_stats(mscd_ctx *ctx, mscd_serve_stats *out);
 
 #ifdef __cplusplus
 }

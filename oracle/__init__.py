@@ -34,6 +34,8 @@ def lib():
         L.orc_grow.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_int64, i32p, C.c_int64, i64p, f64p, i64p]
         L.orc_run.argtypes = [C.c_void_p, f64p, C.c_int32, i32p, C.c_int64, C.c_int64, C.c_int,
                               C.POINTER(C.c_void_p)]
+        L.orc_run_init.argtypes = [C.c_void_p, f64p, C.c_int32, i32p, C.c_int64, i64p, i32p, C.c_int64, C.c_int,
+                                   C.POINTER(C.c_void_p)]
         L.orc_result_destroy.argtypes = [C.c_void_p]
         L.orc_result_sizes.argtypes = [C.c_void_p, i64p]
         L.orc_result_get.argtypes = [C.c_void_p, i64p, i32p, f64p, i64p]
@@ -109,13 +111,22 @@ def grow(g: Graph, seed: int, alpha: float, max_rounds: int = MAX_ROUNDS):
     return buf[: ln.value].copy(), f.value, dict(zip(STAT_FIELDS, st.tolist())), rc
 
 
-def run(g: Graph, alphas, seeds=None, threads: int = 1, max_rounds: int = MAX_ROUNDS):
-    """All units, scale-major.  Returns (status, ptr, nodes, f, stats[U,8])."""
+def run(g: Graph, alphas, seeds=None, threads: int = 1, max_rounds: int = MAX_ROUNDS, init=None):
+    """All units, scale-major.  Returns (status, ptr, nodes, f, stats[U,8]).
+    init: optional (ptr int64[n_seeds+1], nodes int32) initial members per seed."""
     alphas = np.ascontiguousarray(alphas, dtype=np.float64)
     seeds = np.arange(g.n, dtype=np.int32) if seeds is None else np.ascontiguousarray(seeds, dtype=np.int32)
     h = C.c_void_p()
-    rc = lib().orc_run(g.h, _p(alphas, f64p), len(alphas), _p(seeds, i32p), len(seeds), int(max_rounds),
-                       int(threads), C.byref(h))
+    if init is None:
+        rc = lib().orc_run(g.h, _p(alphas, f64p), len(alphas), _p(seeds, i32p), len(seeds), int(max_rounds),
+                           int(threads), C.byref(h))
+    else:
+        iptr = np.ascontiguousarray(init[0], np.int64)
+        inodes = np.ascontiguousarray(init[1], np.int32)
+        if len(inodes) == 0:
+            inodes = np.zeros(1, np.int32)
+        rc = lib().orc_run_init(g.h, _p(alphas, f64p), len(alphas), _p(seeds, i32p), len(seeds), _p(iptr, i64p),
+                                _p(inodes, i32p), int(max_rounds), int(threads), C.byref(h))
     if not h.value:
         return rc, None, None, None, None
     U = len(alphas) * len(seeds)

@@ -388,7 +388,12 @@ struct Grower {
     }
 };
 
-static void grow_unit(const orc_graph &g, i32 seed, double alpha, i64 max_rounds, UnitResult &R) {
+// Alg. 1 repeated while a grow pass adds (Alg. 2), from c = {seed} plus the
+// optional initial members init[0..n_init) (Alg. 2: "a set of initial
+// communities is given"; the seed stays pinned, repeats are ignored, the
+// insertions are not counted as additions).
+static void grow_unit(const orc_graph &g, i32 seed, double alpha, i64 max_rounds, UnitResult &R,
+                      const i32 *init = nullptr, i64 n_init = 0) {
     Grower gr{g, alpha};
     std::unordered_map<i32, i64> din;  // d_in(u, c) for every node touched
     std::unordered_map<i32, char> inC;  // membership
@@ -397,6 +402,15 @@ static void grow_unit(const orc_graph &g, i32 seed, double alpha, i64 max_rounds
     inC[seed] = 1;
     for (i64 e = g.rp[seed]; e < g.rp[seed + 1]; e++) din[g.col[e]] += g.wt(e);
     R.edges_scanned += g.rp[seed + 1] - g.rp[seed];
+    for (i64 j = 0; j < n_init; j++) {
+        const i32 u = init[j];
+        if (member(u)) continue;
+        K += 2 * din[u];
+        V += g.k[u];
+        inC[u] = 1;
+        R.edges_scanned += g.rp[u + 1] - g.rp[u];
+        for (i64 e = g.rp[u]; e < g.rp[u + 1]; e++) din[g.col[e]] += g.wt(e);
+    }
 
     auto cmp = [&](const QEntry &a, const QEntry &b) { return gr.ranks_before(b, a); };
     i64 rounds = 0;
@@ -511,13 +525,23 @@ struct orc_result {
     std::vector<UnitResult> units;
 };
 
-extern "C" int orc_run(const orc_graph *g, const double *alphas, i32 n_scales, const i32 *seeds, i64 n_seeds,
-                       i64 max_rounds, int n_threads, orc_result **out) {
+// init_ptr (int64[n_seeds+1]) / init_nodes: optional initial members per seed.
+extern "C" int orc_run_init(const orc_graph *g, const double *alphas, i32 n_scales, const i32 *seeds, i64 n_seeds,
+                            const i64 *init_ptr, const i32 *init_nodes, i64 max_rounds, int n_threads,
+                            orc_result **out) {
     *out = nullptr;
     for (i32 s = 0; s < n_scales; s++)
         if (!(alphas[s] > 0.0) || !std::isfinite(alphas[s])) return ORC_EINVAL;
     for (i64 i = 0; i < n_seeds; i++)
         if (seeds[i] < 0 || seeds[i] >= g->n) return ORC_EINVAL;
+    if (init_ptr) {
+        if (init_ptr[0] != 0) return ORC_EINVAL;
+        for (i64 i = 0; i < n_seeds; i++) {
+            if (init_ptr[i + 1] < init_ptr[i]) return ORC_EINVAL;
+            for (i64 j = init_ptr[i]; j < init_ptr[i + 1]; j++)
+                if (init_nodes[j] < 0 || init_nodes[j] >= g->n) return ORC_EINVAL;
+        }
+    }
     orc_result *r = new orc_result();
     i64 U = (i64)n_scales * n_seeds;
     r->units.resize(U);
@@ -526,7 +550,12 @@ extern "C" int orc_run(const orc_graph *g, const double *alphas, i32 n_scales, c
         for (;;) {
             i64 u = next.fetch_add(1);
             if (u >= U) break;
-            grow_unit(*g, seeds[u % n_seeds], alphas[u / n_seeds], max_rounds, r->units[u]);
+            const i64 si = u % n_seeds;
+            if (init_ptr)
+                grow_unit(*g, seeds[si], alphas[u / n_seeds], max_rounds, r->units[u], init_nodes + init_ptr[si],
+                          init_ptr[si + 1] - init_ptr[si]);
+            else
+                grow_unit(*g, seeds[si], alphas[u / n_seeds], max_rounds, r->units[u]);
         }
     };
     if (n_threads < 1) n_threads = 1;
@@ -539,6 +568,11 @@ extern "C" int orc_run(const orc_graph *g, const double *alphas, i32 n_scales, c
     for (auto &R : r->units)
         if (R.status != ORC_OK) st = R.status;
     return st;
+}
+
+extern "C" int orc_run(const orc_graph *g, const double *alphas, i32 n_scales, const i32 *seeds, i64 n_seeds,
+                       i64 max_rounds, int n_threads, orc_result **out) {
+    return orc_run_init(g, alphas, n_scales, seeds, n_seeds, nullptr, nullptr, max_rounds, n_threads, out);
 }
 
 extern "C" void orc_result_destroy(orc_result *r) { delete r; }

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <map>
@@ -17,6 +18,7 @@
 #include "common.cuh"
 #include "dedup.cuh"
 #include "grow.cuh"
+#include "ladder.cuh"
 
 namespace {
 
@@ -34,15 +36,21 @@ struct GraphRec {
     i64 max_part_n = 0;       // largest part (= n for one CSR): bounds a community's size
 };
 
-struct Counters {
-    unsigned long long work, out_cursor, out_needed, n_retry_state, n_retry_out;
-    u32 error_flags;
-    u32 pad;
-};
-
 __global__ void check_seeds(const i32 *seeds, i64 N, i64 n, u32 *bad) {
     for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (i64)gridDim.x * blockDim.x)
         if (seeds[i] < 0 || (i64)seeds[i] >= n) atomicOr(bad, 1u);
+}
+
+// Initial member lists: offsets from 0, non-decreasing; node ids in range.
+__global__ void check_init(const i64 *ptr, i64 N, const i32 *nodes, i64 n, u32 *bad) {
+    const i64 stride = (i64)gridDim.x * blockDim.x;
+    const i64 t0 = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t0 == 0 && ptr[0] != 0) atomicOr(bad, 1u);
+    for (i64 i = t0; i < N; i += stride)
+        if (ptr[i + 1] < ptr[i]) atomicOr(bad, 1u);
+    const i64 m = ptr[N];
+    for (i64 j = t0; j < m; j += stride)
+        if (nodes[j] < 0 || (i64)nodes[j] >= n) atomicOr(bad, 1u);
 }
 
 // Column sums of the per-unit statistics and status counts.
@@ -98,6 +106,10 @@ std::atomic<long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+struct Server;
+void serve_destroy(Server *s);
+bool serve_graph_busy(Server *s, int32_t graph_id);
+
 struct mscd_ctx {
     int device = 0;
     int sm_count = 1;
@@ -110,23 +122,24 @@ struct mscd_ctx {
     i64 N = 0, U = 0, n_nodes_graph = 0;
     double *alphas = nullptr;
     i32 *seeds = nullptr;
+    i64 *init_ptr = nullptr;  // initial members per seed (mscd_run_init)
+    i32 *init_nodes = nullptr;
     i64 *uoff = nullptr;
     i32 *ulen = nullptr;
     u64 *uhash = nullptr;
     double *uf = nullptr;
     i64 *ustat = nullptr;
     i32 *ustatus = nullptr;
-    i32 *out_nodes = nullptr;
-    i64 out_cap = 0;
     std::vector<ScaleResult> scales;
     int32_t n_parts = 1;
     std::vector<double> nmi_succ, win3, win5;  // per part: S-1, S and S values
     mscd_run_stats stats{};
     // autotuner results by graph shape class: parameters and growth ms of the sample
     std::map<u64, std::pair<mscd_params, double>> tune_cache;
-    // reusable growth arena
-    unsigned char *arena = nullptr;
-    size_t arena_bytes = 0;
+    // the growth pipeline of runs: its arena, retry lists and output buffer are reused
+    GrowPipe pipe;
+    Server *server = nullptr;  // query serving (mscd_serve_start)
+    char last_error[160] = "";  // where the last failed run stopped
 };
 
 namespace {
@@ -134,6 +147,10 @@ namespace {
 void free_run(mscd_ctx *c) {
     cudaFree(c->alphas);
     cudaFree(c->seeds);
+    cudaFree(c->init_ptr);
+    cudaFree(c->init_nodes);
+    c->init_ptr = nullptr;
+    c->init_nodes = nullptr;
     cudaFree(c->uoff);
     cudaFree(c->ulen);
     cudaFree(c->uhash);
@@ -174,32 +191,6 @@ GraphRec *find_graph(mscd_ctx *c, int32_t id) {
     return &c->graphs[id];
 }
 
-int ensure_arena(mscd_ctx *c, size_t bytes) {
-    if (c->arena_bytes >= bytes) return MSCD_OK;
-    cudaFree(c->arena);
-    c->arena = nullptr;
-    c->arena_bytes = 0;
-    MSCD_CUDA(cudaMalloc((void **)&c->arena, bytes));
-    c->arena_bytes = bytes;
-    return MSCD_OK;
-}
-
-// Enlarge the unit output buffer (kept across runs), preserving its first
-// `keep` entries.
-int grow_output(mscd_ctx *c, i64 need, i64 keep, cudaStream_t st) {
-    if (need <= c->out_cap) return MSCD_OK;
-    i64 cap = std::max<i64>(need + need / 8, c->out_cap + c->out_cap / 2);
-    i32 *nb = nullptr;
-    MSCD_CUDA(cudaMalloc((void **)&nb, (size_t)cap * sizeof(i32)));
-    if (c->out_nodes && keep > 0)
-        MSCD_CUDA(cudaMemcpyAsync(nb, c->out_nodes, (size_t)keep * sizeof(i32), cudaMemcpyDeviceToDevice, st));
-    MSCD_CUDA(cudaStreamSynchronize(st));
-    cudaFree(c->out_nodes);
-    c->out_nodes = nb;
-    c->out_cap = cap;
-    return MSCD_OK;
-}
-
 void window_means(const std::vector<double> &nmi, int32_t S, int p, std::vector<double> &out) {
     out.assign(S, NAN);
     for (int32_t i = 0; i < S; ++i) {
@@ -216,11 +207,6 @@ void window_means(const std::vector<double> &nmi, int32_t S, int p, std::vector<
     }
 }
 
-struct Task {
-    int cls;                 // index in the node-slot class ladder
-    std::vector<i64> units;  // the listed units, unless `all` (every unit of the scale group)
-    bool all;
-};
 
 }  // namespace
 
@@ -231,6 +217,20 @@ bool ctx_graph(mscd_ctx *c, int32_t graph_id, DevGraph *g, int *device) {
     *device = c->device;
     return true;
 }
+
+Server **ctx_server(mscd_ctx *c) { return &c->server; }
+
+bool ctx_graph_part(mscd_ctx *c, int32_t id, DevGraph *g, i64 *max_part_n) {
+    GraphRec *r = find_graph(c, id);
+    if (!r) return false;
+    *g = r->g;
+    *max_part_n = r->max_part_n;
+    return true;
+}
+
+int ctx_device_of(mscd_ctx *c) { return c->device; }
+int ctx_sm_count_of(mscd_ctx *c) { return c->sm_count; }
+mscd_params ctx_params_of(mscd_ctx *c) { return c->p; }
 
 extern "C" {
 
@@ -250,6 +250,7 @@ const char *mscd_strerror(int s) {
     case MSCD_EUNSORTED: return "CSR row not in ascending column order";
     case MSCD_EWEIGHT: return "edge weight not finite and positive";
     case MSCD_ENORESULT: return "no successful run to read results from";
+    case MSCD_EBUSY: return "in use (a graph that queries still need, or a running server)";
     default: return "unknown status";
     }
 }
@@ -287,6 +288,7 @@ int mscd_create(mscd_ctx **out, int device, const mscd_params *params) {
         return MSCD_EINVAL;
     }
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    c->pipe.sm_count = c->sm_count;
     if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) {
         delete c;
         return MSCD_EDEVICE;
@@ -297,12 +299,13 @@ int mscd_create(mscd_ctx **out, int device, const mscd_params *params) {
 
 int mscd_destroy(mscd_ctx *c) {
     if (!c) return MSCD_EINVAL;
+    serve_destroy(c->server);
+    c->server = nullptr;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->own);
     free_run(c);
     for (auto &g : c->graphs) free_graph(g);
-    cudaFree(c->arena);
-    cudaFree(c->out_nodes);
+    pipe_free(c->pipe);
     cudaStreamDestroy(c->own);
     delete c;
     return MSCD_OK;
@@ -409,6 +412,7 @@ extern "C" {
 int mscd_graph_free(mscd_ctx *c, int32_t graph_id) {
     GraphRec *g = find_graph(c, graph_id);
     if (!g) return MSCD_EINVAL;
+    if (serve_graph_busy(c->server, graph_id)) return MSCD_EBUSY;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->own);
     free_graph(*g);
@@ -450,7 +454,8 @@ namespace {
 
 // The whole path of mscd_run; growth_only stops after the growth (autotuning).
 int run_impl(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scales, const int32_t *seeds,
-             int64_t n_seeds, uint32_t flags, void *cuda_stream, bool growth_only) {
+             int64_t n_seeds, uint32_t flags, void *cuda_stream, bool growth_only, const int64_t *init_ptr = nullptr,
+             const int32_t *init_nodes = nullptr) {
     GraphRec *gr = find_graph(c, graph_id);
     if (!gr || !alphas || n_scales < 1) return MSCD_EINVAL;
     MSCD_CUDA(cudaSetDevice(c->device));
@@ -474,8 +479,8 @@ int run_impl(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
     cudaEvent_t ev[4];
     for (auto &e : ev) cudaEventCreate(&e);
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> dedup_ev;  // around each group's dedup
-    Counters *ctr = nullptr;
-    i64 *retry_a = nullptr, *retry_b = nullptr;
+    char stage[96];
+    snprintf(stage, sizeof(stage), "setup");
     unsigned char *big_seed = nullptr;
     int rc = MSCD_OK;
     cudaEventRecord(ev[0], st);
@@ -497,228 +502,95 @@ int run_impl(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
         if ((rc = cuda_status(cudaMalloc((void **)&c->uf, U1 * sizeof(double))))) break;
         if ((rc = cuda_status(cudaMalloc((void **)&c->ustat, U1 * MSCD_NSTATS * sizeof(i64))))) break;
         if ((rc = cuda_status(cudaMalloc((void **)&c->ustatus, U1 * sizeof(i32))))) break;
-        if ((rc = cuda_status(cudaMalloc((void **)&ctr, sizeof(Counters))))) break;
-        if ((rc = cuda_status(cudaMalloc((void **)&retry_a, U1 * sizeof(i64))))) break;
-        if ((rc = cuda_status(cudaMalloc((void **)&retry_b, U1 * sizeof(i64))))) break;
+        c->pipe.st = st;
+        if ((rc = pipe_reserve(c->pipe, (i64)U1))) break;
+        Counters *ctr = c->pipe.ctr;
         if ((rc = cuda_status(cudaMalloc((void **)&big_seed, (size_t)std::max<i64>(N, 1))))) break;
         if ((rc = cuda_status(cudaMemsetAsync(big_seed, 0, (size_t)std::max<i64>(N, 1), st)))) break;
+        if (init_ptr && N > 0) {
+            // initial member lists (copied; checked on the device below)
+            i64 m = 0;
+            if (dev) MSCD_CUDA(cudaMemcpy(&m, init_ptr + N, sizeof(i64), cudaMemcpyDeviceToHost));
+            else m = init_ptr[N];
+            if (m < 0 || (m > 0 && !init_nodes)) { rc = MSCD_EINVAL; break; }
+            const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+            if ((rc = cuda_status(cudaMalloc((void **)&c->init_ptr, (N + 1) * sizeof(i64))))) break;
+            if ((rc = cuda_status(cudaMalloc((void **)&c->init_nodes, (size_t)std::max<i64>(m, 1) * sizeof(i32)))))
+                break;
+            if ((rc = cuda_status(cudaMemcpyAsync(c->init_ptr, init_ptr, (N + 1) * sizeof(i64), kind, st)))) break;
+            if (m > 0 && (rc = cuda_status(cudaMemcpyAsync(c->init_nodes, init_nodes, m * sizeof(i32), kind, st))))
+                break;
+        }
         if (c->seeds) {
             if ((rc = cuda_status(cudaMemsetAsync(ctr, 0, sizeof(Counters), st)))) break;
             check_seeds<<<152 * 8, 256, 0, st>>>(c->seeds, N, G.n, &ctr->error_flags); note_launch();
+            if (c->init_ptr) {
+                check_init<<<152 * 8, 256, 0, st>>>(c->init_ptr, N, c->init_nodes, G.n, &ctr->error_flags);
+                note_launch();
+            }
             u32 bad = 0;
             if ((rc = cuda_status(cudaMemcpyAsync(&bad, &ctr->error_flags, sizeof(u32), cudaMemcpyDeviceToHost, st))))
                 break;
             if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
             if (bad) { rc = MSCD_EINVAL; break; }
         }
-        // ---- growth: a task list of (slot class, units) ----
-        // Node-slot classes, one unit per warp: a shared-memory class of
-        // smem_slots (1024) and optionally one of mid_slots; then global-memory
-        // arenas of 8x the capacity per class, up to the first power of two
-        // above the node count (never overflows), run at global_warps_per_sm.
+        // ---- growth ----
         std::vector<int> ladder;
         std::vector<bool> in_smem;
-        {
-            const size_t smem_budget = 220 * 1024;
-            int c0 = c->p.smem_slots;
-            if (c0 == 0) c0 = grow_state_bytes(G, 1024) * 4 <= smem_budget ? 1024 : 512;
-            if (grow_state_bytes(G, c0) > smem_budget) {  // one unit's slots must fit a CTA
-                rc = MSCD_EINVAL;
-                break;
-            }
-            ladder.push_back(c0);
-            if (c->p.mid_slots > ladder.back() && grow_state_bytes(G, c->p.mid_slots) <= smem_budget)
-                ladder.push_back(c->p.mid_slots);
-            in_smem.assign(ladder.size(), true);
-            // a community stays inside its seed's part: the part size bounds it
-            i64 full = 32;
-            while (full < gr->max_part_n + 1) full <<= 1;
-            i64 cg = ladder.back();
-            if (c->p.global_slots > cg && cg < full) {
-                cg = std::min<i64>(c->p.global_slots, full);
-                ladder.push_back((int)cg);
-                in_smem.push_back(false);
-            }
-            while (cg < full) {
-                cg = std::min<i64>(cg * 8, full);
-                ladder.push_back((int)cg);
-                in_smem.push_back(false);
-            }
-        }
+        if ((rc = make_ladder(G, gr->max_part_n, c->p, &ladder, &in_smem))) break;
         // Scale groups.  The member lists of a group's units go to one output
         // buffer; once the group is grown, each of its scales is deduplicated
         // and its units are pointed at their community's list (the lists are
         // equal), so the buffer is free again for the next group.  A group is
-        // as many scales as fit a quarter of the free memory at the expected
-        // list length (the last group's mean, with a margin); the persistent
-        // schedule usually needs one group, the plain form takes one scale at
-        // a time.  Within a group: a task list of (slot class, units).
+        // as many scales as fit 40% of the free memory at the expected list
+        // length (1024 entries per unit at first, then twice the last group's
+        // mean); the persistent schedule usually needs one group, the plain
+        // form takes one scale at a time.
         const bool per_scale = c->p.schedule == MSCD_SCHED_PER_SCALE;
         size_t free_mem = 0, total_mem = 0;
         cudaMemGetInfo(&free_mem, &total_mem);
-        const i64 out_budget = (i64)(free_mem / 4 / sizeof(i32));  // output may take a quarter of free memory
-        double per_unit = std::max(1.0, std::min<double>(256.0, (double)gr->max_part_n));
+        i64 out_budget = (i64)(free_mem / 10 * 4 / sizeof(i32));
+        double per_unit = std::max(1.0, std::min<double>(1024.0, (double)gr->max_part_n));
+        GrowArgs proto{};
+        proto.G = G;
+        proto.alphas = c->alphas;
+        proto.seeds = c->seeds;
+        proto.n_seeds = N;
+        proto.max_rounds = c->p.max_rounds;
+        proto.uoff = c->uoff;
+        proto.ulen = c->ulen;
+        proto.uhash = c->uhash;
+        proto.uf = c->uf;
+        proto.ustat = c->ustat;
+        proto.ustatus = c->ustatus;
+        proto.big_seed = c->init_ptr ? nullptr : big_seed;  // sizes from {seed} do not predict these
+        proto.init_ptr = c->init_ptr;
+        proto.init_nodes = c->init_nodes;
+        proto.log_kmax = G.kmax > 1 ? (float)std::log((double)G.kmax) : 0.0f;
+        c->pipe.p = c->p;
+        c->pipe.st = st;
+        c->pipe.stats = &c->stats;
         int32_t s0 = 0;
         while (s0 < n_scales && rc == MSCD_OK) {
+        {
+            // 35% of what is free, counting the output buffer being reused
+            size_t fr = 0, tot = 0;
+            cudaMemGetInfo(&fr, &tot);
+            out_budget = (i64)((double)(fr + (size_t)c->pipe.out_cap * sizeof(i32)) * 0.35 / sizeof(i32));
+        }
         int32_t s1 = s0 + 1;
         if (!per_scale && N > 0)
             s1 = (int32_t)std::min<i64>(n_scales, s0 + std::max<i64>(1, (i64)(out_budget / (per_unit * N))));
         else if (!per_scale)
             s1 = n_scales;
         const i64 group_units = (i64)(s1 - s0) * N;
-        std::vector<Task> tasks;
-        if (group_units > 0) tasks.push_back(Task{0, {}, true});
         unsigned long long cursor = 0;
-        while (!tasks.empty() && rc == MSCD_OK) {
-            Task t = std::move(tasks.front());
-            tasks.erase(tasks.begin());
-            const int cap = ladder[t.cls];
-            const bool sm = in_smem[t.cls];
-            const i64 n_work = t.all ? group_units : (i64)t.units.size();
-            // room for every list this launch can write (<= min(cap, n) each) when
-            // that fits the budget; otherwise units that find it full are retried
-            {
-                const i64 bound = (i64)cursor + n_work * std::min<i64>(cap, std::max<i64>(gr->max_part_n, 1));
-                const i64 want = std::min<i64>(bound, std::max<i64>(out_budget, (i64)cursor + n_work * 64));
-                if ((rc = grow_output(c, want, (i64)cursor, st))) break;
-            }
-            if ((rc = cuda_status(cudaMemsetAsync(ctr, 0, sizeof(Counters), st)))) break;
-            GrowArgs a{};
-            a.G = G;
-            a.alphas = c->alphas;
-            a.seeds = c->seeds;
-            a.n_seeds = N;
-            a.n_work = n_work;
-            a.work_counter = &ctr->work;
-            a.plain = per_scale ? 1 : 0;
-            a.unit_base = t.all ? (i64)s0 * N : 0;
-            a.cap = cap;
-            a.max_rounds = c->p.max_rounds;
-            a.out_nodes = c->out_nodes;
-            a.out_cursor = &ctr->out_cursor;
-            a.out_needed = &ctr->out_needed;
-            a.out_cap = c->out_cap;
-            a.uoff = c->uoff;
-            a.ulen = c->ulen;
-            a.uhash = c->uhash;
-            a.uf = c->uf;
-            a.ustat = c->ustat;
-            a.ustatus = c->ustatus;
-            a.retry_state = retry_a;
-            a.n_retry_state = &ctr->n_retry_state;
-            a.retry_out = retry_b;
-            a.n_retry_out = &ctr->n_retry_out;
-            a.error_flags = &ctr->error_flags;
-            a.state_bytes = grow_state_bytes(G, cap);
-            a.big_seed = t.cls == 0 ? big_seed : nullptr;
-            a.log_kmax = G.kmax > 1 ? (float)std::log((double)G.kmax) : 0.0f;
-            i64 *list_dev = nullptr;
-            if (!t.all) {
-                if ((rc = cuda_status(cudaMallocAsync((void **)&list_dev, n_work * sizeof(i64), st)))) break;
-                if ((rc = cuda_status(cudaMemcpyAsync(list_dev, t.units.data(), n_work * sizeof(i64),
-                                                      cudaMemcpyHostToDevice, st))))
-                    break;
-                a.work_list = list_dev;
-            }
-            // unit lists are appended after everything earlier launches wrote
-            if ((rc = cuda_status(cudaMemcpyAsync(&ctr->out_cursor, &cursor, sizeof(cursor), cudaMemcpyHostToDevice,
-                                                  st))))
-                break;
-            int blocks = 0, threads = 32;
-            size_t smem = 0;
-            i64 chunk = n_work;  // work items per launch (the plain form's arena bounds it)
-            if (sm) {
-                // as many one-warp units per CTA as fit 220 KiB (<= 16), one CTA per SM
-                a.use_smem = 1;
-                const int wpc = (int)std::max<size_t>(1, std::min<size_t>(16, (220 * 1024) / a.state_bytes));
-                threads = 32 * wpc;
-                smem = (size_t)wpc * a.state_bytes;
-                int per_sm = 0;
-                if ((rc = grow_occupancy(a, threads, smem, &per_sm))) break;
-                if (t.cls == 0 && c->p.blocks_per_sm > 0) per_sm = std::min(per_sm, c->p.blocks_per_sm);
-                if (per_sm < 1) { rc = MSCD_EINVAL; break; }
-                blocks = per_sm * c->sm_count;
-            } else {
-                a.use_smem = 0;
-                const int wpc = GLOBAL_CTA_THREADS / 32;
-                // group bounds (8 bytes per 32 slots and unit) in shared memory when small
-                if (cap <= 16384) {
-                    a.bounds_smem = 1;
-                    smem = (size_t)wpc * 8 * (size_t)(cap / 32);
-                }
-                const size_t budget = (size_t)4 << 30;
-                i64 warps = std::max<i64>(
-                    1, std::min<i64>((i64)(budget / a.state_bytes), (i64)c->sm_count * c->p.global_warps_per_sm));
-                if (per_scale) warps = (i64)(budget / a.state_bytes);
-                warps = std::max<i64>(1, std::min<i64>(warps, std::max<i64>(n_work, 1)));
-                if (per_scale) chunk = warps;
-                threads = (int)std::min<i64>(warps, wpc) * 32;
-                blocks = (int)((warps + threads / 32 - 1) / (threads / 32));
-                if ((rc = ensure_arena(c, (size_t)blocks * (threads / 32) * a.state_bytes))) break;
-                a.gstate = c->arena;
-            }
-            blocks = (int)std::max<i64>(1, std::min<i64>(blocks, (n_work + threads / 32 - 1) / (threads / 32)));
-            cudaEvent_t l0, l1;
-            cudaEventCreate(&l0);
-            cudaEventCreate(&l1);
-            cudaEventRecord(l0, st);
-            if (!per_scale) {
-                rc = grow_launch(a, blocks, threads, smem, st);
-            } else {
-                // one statically mapped unit per warp: a grid over the items
-                const int wpc = threads / 32;
-                for (i64 b = 0; b < n_work && rc == MSCD_OK; b += chunk) {
-                    a.work_base = b;
-                    const i64 items = std::min<i64>(chunk, n_work - b);
-                    rc = grow_launch(a, (int)((items + wpc - 1) / wpc), threads, smem, st);
-                }
-            }
-            if (rc) break;
-            cudaEventRecord(l1, st);
-            Counters h{};
-            if ((rc = cuda_status(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st)))) break;
-            if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
-            if (c->stats.grow_launches < 8) {
-                const int r = (int)c->stats.grow_launches;
-                float lms = 0.0f;
-                cudaEventElapsedTime(&lms, l0, l1);
-                c->stats.launch_cap[r] = cap;
-                c->stats.launch_smem[r] = sm ? 1 : 0;
-                c->stats.launch_units[r] = n_work;
-                c->stats.launch_ms[r] = lms;
-            }
-            cudaEventDestroy(l0);
-            cudaEventDestroy(l1);
-            c->stats.grow_launches++;
-            if (list_dev) cudaFree(list_dev);
-            if (h.error_flags) { rc = MSCD_EDEVICE; break; }
-            if (!h.n_retry_out) {
-                cursor = h.out_cursor;
-            } else {
-                // Reservations are taken in increasing order and every list is
-                // non-empty, so once one fails all later ones fail: every
-                // written list lies below the old capacity.
-                std::vector<i64> lst(h.n_retry_out);
-                if ((rc = cuda_status(cudaMemcpy(lst.data(), retry_b, lst.size() * sizeof(i64),
-                                                 cudaMemcpyDeviceToHost))))
-                    break;
-                cursor = (unsigned long long)c->out_cap;
-                if ((rc = grow_output(c, c->out_cap + (i64)h.out_needed + (1 << 20), (i64)cursor, st))) break;
-                tasks.insert(tasks.begin(), Task{t.cls, std::move(lst), false});
-            }
-            if (h.n_retry_state) {
-                std::vector<i64> lst(h.n_retry_state);
-                if ((rc = cuda_status(cudaMemcpy(lst.data(), retry_a, lst.size() * sizeof(i64),
-                                                 cudaMemcpyDeviceToHost))))
-                    break;
-                c->stats.overflow_units += (i64)lst.size();
-                if (t.cls + 1 >= (int)ladder.size()) { rc = MSCD_EDEVICE; break; }
-                tasks.push_back(Task{t.cls + 1, std::move(lst), false});
-            }
-        }
+        proto.unit_base = (i64)s0 * N;
+        snprintf(stage, sizeof(stage), "growth of scales %d..%d", s0, s1 - 1);
+        rc = grow_units(c->pipe, proto, group_units, ladder, in_smem, per_scale, out_budget, gr->max_part_n, &cursor);
         if (rc) break;
         if (group_units > 0)
-            per_unit = std::max(per_unit, 1.25 * (double)cursor / (double)group_units);
+            per_unit = std::max(1.0, 2.0 * (double)cursor / (double)group_units);
         if (!growth_only) {
             // dedup the group's scales; point their units at the community lists
             cudaEvent_t d0, d1;
@@ -728,8 +600,9 @@ int run_impl(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
             cudaEventRecord(d0, st);
             c->scales.resize(n_scales);
             for (int32_t s = s0; s < s1 && rc == MSCD_OK; ++s) {
-                rc = dedup_scale(c->uoff + s * N, c->ulen + s * N, c->uhash + s * N, c->uf + s * N, c->out_nodes, N,
-                                 &c->scales[s], st);
+                snprintf(stage, sizeof(stage), "dedup of scale %d", s);
+                rc = dedup_scale(c->uoff + s * N, c->ulen + s * N, c->uhash + s * N, c->uf + s * N,
+                                 c->pipe.out_nodes, N, &c->scales[s], st);
                 if (rc == MSCD_OK && N > 0) {
                     point_units<<<152 * 4, 256, 0, st>>>(c->scales[s].seed2comm, c->scales[s].comm_ptr, N,
                                                           c->uoff + s * N); note_launch();
@@ -740,6 +613,9 @@ int run_impl(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
         s0 = s1;
         }  // scale groups
         if (rc) break;
+        // a large output buffer is not kept past the growth (the lists now live
+        // in the deduplicated communities)
+        if (!growth_only && c->pipe.out_cap > ((i64)1 << 28)) pipe_release_output(c->pipe);
         cudaEventRecord(ev[1], st);
         // ---- totals ----
         unsigned long long *tot = nullptr;
@@ -779,6 +655,7 @@ int run_impl(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
         {
             std::vector<double> pn(P);
             for (int32_t s = 0; s + 1 < n_scales && rc == MSCD_OK; ++s) {
+                snprintf(stage, sizeof(stage), "stability between scales %d and %d", s, s + 1);
                 rc = nmi_between(c->scales[s], c->scales[s + 1], G.n, gr->part_off, P, pn.data(), st);
                 for (int32_t p = 0; p < P; ++p) c->nmi_succ[(size_t)p * S1 + s] = pn[p];
             }
@@ -813,9 +690,6 @@ int run_impl(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
         else if (n_timeout) rc = MSCD_ETIMEOUT;
     } while (0);
     cudaStreamSynchronize(st);
-    cudaFree(ctr);
-    cudaFree(retry_a);
-    cudaFree(retry_b);
     cudaFree(big_seed);
     for (auto &e : ev) cudaEventDestroy(e);
     for (auto &d : dedup_ev) {
@@ -823,6 +697,8 @@ int run_impl(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
         cudaEventDestroy(d.second);
     }
     if (rc != MSCD_OK && !c->have) free_run(c);
+    if (rc != MSCD_OK)
+        snprintf(c->last_error, sizeof(c->last_error), "mscd_run: %s: %s", stage, mscd_strerror(rc));
     return rc;
 }
 
@@ -840,6 +716,13 @@ extern "C" {
 int mscd_run(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scales, const int32_t *seeds,
              int64_t n_seeds, uint32_t flags, void *cuda_stream) {
     return run_impl(c, graph_id, alphas, n_scales, seeds, n_seeds, flags, cuda_stream, false);
+}
+
+int mscd_run_init(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scales, const int32_t *seeds,
+                  int64_t n_seeds, const int64_t *init_ptr, const int32_t *init_nodes, uint32_t flags,
+                  void *cuda_stream) {
+    if (!seeds || !init_ptr) return MSCD_EINVAL;
+    return run_impl(c, graph_id, alphas, n_scales, seeds, n_seeds, flags, cuda_stream, false, init_ptr, init_nodes);
 }
 
 int mscd_autotune(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scales, int64_t n_sample,
@@ -1003,6 +886,8 @@ int mscd_get_stability_part(mscd_ctx *c, int32_t part, double *nmi_succ, double 
 int mscd_get_stability(mscd_ctx *c, double *nmi_succ, double *nmi_win3, double *nmi_win5) {
     return mscd_get_stability_part(c, 0, nmi_succ, nmi_win3, nmi_win5);
 }
+
+const char *mscd_last_error(mscd_ctx *c) { return c ? c->last_error : ""; }
 
 int mscd_get_run_stats(mscd_ctx *c, mscd_run_stats *out) {
     if (!c || !out) return MSCD_EINVAL;

@@ -446,8 +446,10 @@ __device__ void expand(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Uni
     U.edges += re - rs;
 }
 
+// Add slot s to the community (an addition of the grow pass, or an initial
+// member, which is not counted as one).
 template <class VT, class HT, bool WEIGHTED>
-__device__ void accept(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Unit &U, int s) {
+__device__ void accept(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Unit &U, int s, bool counted = true) {
     const i64 d = st.din[s], kd = st.kdeg[s];
     __syncwarp();
     if ((threadIdx.x & 31) == 0) {
@@ -457,7 +459,7 @@ __device__ void accept(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Uni
     __syncwarp();
     U.K += 2 * d;
     U.V += kd;
-    U.adds++;
+    if (counted) U.adds++;
     expand(st, a, U, s, +1, true);
 }
 
@@ -602,8 +604,8 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
     const int lane = threadIdx.x & 31;
     const DevGraph &G = a.G;
     Unit U;
-    const i64 si = unit % a.n_seeds;
-    U.alpha = a.alphas[unit / a.n_seeds];
+    const i64 si = a.unit_alpha ? unit : unit % a.n_seeds;
+    U.alpha = a.unit_alpha ? a.unit_alpha[unit] : a.alphas[unit / a.n_seeds];
     U.alpha32 = (float)U.alpha;
     U.seed = a.seeds ? a.seeds[si] : (i32)si;
     U.E2 = 2.0f * 0x1p-20f * (1.0f + U.alpha32) * (1.0f + a.log_kmax);
@@ -629,6 +631,17 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
     if (lane == 0) st.flag[0] = F_MEMBER;
     __syncwarp();
     expand(st, a, U, 0, +1, false);
+    if (a.init_ptr) {
+        // initial members (Alg. 2 may start from given communities); repeats
+        // and the seed itself are skipped
+        for (i64 j = a.init_ptr[si]; j < a.init_ptr[si + 1] && !U.ovf && !U.err; ++j) {
+            int s = lookup_insert(st, G, U, a.init_nodes[j], lane == 0);
+            if (U.ovf || U.err) break;
+            s = __shfl_sync(FULL_MASK, s, 0);
+            if (st.flag[s] & F_MEMBER) continue;
+            accept(st, a, U, s, false);
+        }
+    }
 
     while (!U.ovf && !U.err) {
         if (U.rounds >= a.max_rounds) {

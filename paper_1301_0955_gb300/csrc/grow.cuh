@@ -11,6 +11,12 @@ struct GrowArgs {
     const double *alphas;   // [n_scales]
     const i32 *seeds;       // [n_seeds] or null = node ids 0..n_seeds-1
     i64 n_seeds;
+    // per-unit scales (serving batches mix queries): unit u grows from
+    // seeds[u] at unit_alpha[u]; null = unit u is (scale u / n_seeds, seed u % n_seeds)
+    const double *unit_alpha;
+    // optional initial members per seed index (init_ptr[si]..init_ptr[si+1])
+    const i64 *init_ptr;
+    const i32 *init_nodes;
     // work: units 0..n_work-1, or the listed units
     const i64 *work_list;
     i64 n_work;

@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_PKG, "lib", "libmscd.so")
 
 OK = 0
 EINVAL, ENOTSYM, ESELFLOOP, EDUP, ERANGE, ENOMEM, EDEVICE = -1, -2, -3, -4, -5, -6, -7
-ETIMEOUT, ESMALL, EUNDECIDED, EUNSORTED, EWEIGHT, ENORESULT = -8, -9, -10, -11, -12, -13
+ETIMEOUT, ESMALL, EUNDECIDED, EUNSORTED, EWEIGHT, ENORESULT, EBUSY = -8, -9, -10, -11, -12, -13, -14
+Q_QUEUED, Q_RUNNING, Q_DONE = 0, 1, 2
 DEVICE_PTRS = 1
 SCHED_PERSISTENT = 0
 SCHED_PER_SCALE = 1
@@ -38,6 +39,16 @@ class mscd_params(C.Structure):
                 ("blocks_per_sm", C.c_int32), ("mid_slots", C.c_int32), ("global_warps_per_sm", C.c_int32),
                 ("global_slots", C.c_int32), ("max_rounds", C.c_int64), ("schedule", C.c_int32),
                 ("reserved", C.c_int32)]
+
+
+class mscd_serve_params(C.Structure):
+    _fields_ = [("struct_size", C.c_int32), ("workers", C.c_int32), ("max_batch_units", C.c_int64),
+                ("memory_budget", C.c_int64)]
+
+
+class mscd_serve_stats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("queries_submitted", "queries_done", "units_done", "batches", "queued",
+                                         "in_flight_bytes", "max_in_flight_bytes", "budget_bytes")]
 
 
 class mscd_run_stats(C.Structure):
@@ -69,15 +80,24 @@ SIGNATURES = {
     "mscd_graph_degrees": (C.c_int, [vp, C.c_int32, i64p]),
     "mscd_scales_logspaced": (C.c_int, [C.c_double, C.c_double, C.c_int32, f64p]),
     "mscd_run": (C.c_int, [vp, C.c_int32, vp, C.c_int32, vp, C.c_int64, C.c_uint32, vp]),
+    "mscd_run_init": (C.c_int, [vp, C.c_int32, vp, C.c_int32, vp, C.c_int64, vp, vp, C.c_uint32, vp]),
     "mscd_get_membership": (C.c_int, [vp, C.c_int32, C.c_int64, i32p, C.c_int64, i64p, f64p]),
     "mscd_get_memberships": (C.c_int, [vp, C.c_int32, i64p, i32p, C.c_int64, f64p, i64p, i64p]),
     "mscd_get_communities": (C.c_int, [vp, C.c_int32, i64p, C.c_int64, i32p, C.c_int64, f64p, i32p, i64p, i64p]),
     "mscd_get_stability": (C.c_int, [vp, f64p, f64p, f64p]),
     "mscd_get_stability_part": (C.c_int, [vp, C.c_int32, f64p, f64p, f64p]),
     "mscd_autotune": (C.c_int, [vp, C.c_int32, f64p, C.c_int32, C.c_int64, C.c_uint32, C.POINTER(mscd_params), f64p]),
+    "mscd_serve_start": (C.c_int, [vp, C.POINTER(mscd_serve_params)]),
+    "mscd_serve_stop": (C.c_int, [vp]),
+    "mscd_query_submit": (C.c_int, [vp, C.c_int32, i32p, C.c_int32, C.c_double, C.POINTER(C.c_uint64)]),
+    "mscd_query_poll": (C.c_int, [vp, C.c_uint64, i32p]),
+    "mscd_query_wait": (C.c_int, [vp, C.c_uint64, C.c_int64, i32p]),
+    "mscd_query_result": (C.c_int, [vp, C.c_uint64, i64p, i32p, C.c_int64, f64p, i64p, f64p]),
+    "mscd_serve_get_stats": (C.c_int, [vp, C.POINTER(mscd_serve_stats)]),
     "mscd_graph_union": (C.c_int, [vp, i32p, C.c_int32, i32p]),
     "mscd_graph_parts": (C.c_int, [vp, C.c_int32, i64p, C.c_int32, i32p]),
     "mscd_get_run_stats": (C.c_int, [vp, C.POINTER(mscd_run_stats)]),
+    "mscd_last_error": (C.c_char_p, [vp]),
     "mscd_grow_noalloc": (C.c_int, [vp, C.c_int32, f64p, C.c_int32, vp, C.c_int64, vp, C.c_int64, vp, vp, vp, vp,
                                     vp, vp, i64p, vp]),
 }
@@ -192,6 +212,53 @@ class Context:
                                     C.byref(p), C.byref(ms)), "mscd_autotune")
         return {k: getattr(p, k) for k, _ in mscd_params._fields_}, ms.value
 
+    # ---- serving
+    def serve_start(self, workers: int = 0, max_batch_units: int = 0, memory_budget: int = 0):
+        p = mscd_serve_params(C.sizeof(mscd_serve_params), workers, max_batch_units, memory_budget)
+        _check(load().mscd_serve_start(self.h, C.byref(p)), "mscd_serve_start")
+
+    def serve_stop(self):
+        _check(load().mscd_serve_stop(self.h), "mscd_serve_stop")
+
+    def submit(self, gid: int, seeds, alpha: float) -> int:
+        seeds = np.ascontiguousarray(seeds, np.int32)
+        q = C.c_uint64()
+        _check(load().mscd_query_submit(self.h, gid, seeds.ctypes.data_as(i32p), len(seeds), float(alpha),
+                                        C.byref(q)), "mscd_query_submit")
+        return q.value
+
+    def poll(self, qid: int) -> int:
+        st = C.c_int32()
+        _check(load().mscd_query_poll(self.h, qid, C.byref(st)), "mscd_query_poll")
+        return st.value
+
+    def wait(self, qid: int, timeout_s: float = 60.0) -> int:
+        st = C.c_int32()
+        _check(load().mscd_query_wait(self.h, qid, int(timeout_s * 1e6), C.byref(st)), "mscd_query_wait")
+        return st.value
+
+    def result(self, qid: int, n_seeds: int):
+        """(ptr, nodes, fitness, times_ms, status) of a done query; releases it."""
+        L = load()
+        nn = C.c_int64()
+        times = np.zeros(3, np.float64)
+        rc = L.mscd_query_result(self.h, qid, None, None, 0, None, C.byref(nn), None)
+        if rc != ESMALL:
+            _check(rc, "mscd_query_result")
+        ptr = np.zeros(n_seeds + 1, np.int64)
+        nodes = np.zeros(max(nn.value, 1), np.int32)
+        f = np.zeros(n_seeds, np.float64)
+        rc = L.mscd_query_result(self.h, qid, ptr.ctypes.data_as(i64p), nodes.ctypes.data_as(i32p), len(nodes),
+                                 f.ctypes.data_as(f64p), C.byref(nn), times.ctypes.data_as(f64p))
+        if rc not in (OK, ETIMEOUT, EUNDECIDED):
+            raise MscdError(rc, "mscd_query_result")
+        return ptr, nodes[: nn.value], f, times, rc
+
+    def serve_stats(self) -> dict:
+        st = mscd_serve_stats()
+        _check(load().mscd_serve_get_stats(self.h, C.byref(st)), "mscd_serve_get_stats")
+        return {k: getattr(st, k) for k, _ in mscd_serve_stats._fields_}
+
     def graph_union(self, gids) -> int:
         """Disjoint union of resident graphs as one resident graph (batching)."""
         ids = np.ascontiguousarray(gids, np.int32)
@@ -240,9 +307,25 @@ class Context:
             st = stream if isinstance(stream, int) else stream.cuda_stream
         rc = load().mscd_run(self.h, gid, ap, n_scales, sp, n_seeds, DEVICE_PTRS if dev else 0, st)
         if rc not in (OK, ETIMEOUT, EUNDECIDED):
-            raise MscdError(rc, "mscd_run")
+            raise MscdError(rc, load().mscd_last_error(self.h).decode() or "mscd_run")
         self.n_scales = n_scales
         self.n_seeds = n_seeds if seeds is not None else self.graph_info(gid)["n"]
+        return rc
+
+    def run_init(self, gid: int, alphas, seeds, init_ptr, init_nodes) -> int:
+        """mscd_run from seeds plus initial members (host arrays)."""
+        alphas = np.ascontiguousarray(alphas, np.float64)
+        seeds = np.ascontiguousarray(seeds, np.int32)
+        init_ptr = np.ascontiguousarray(init_ptr, np.int64)
+        init_nodes = np.ascontiguousarray(init_nodes, np.int32)
+        if len(init_nodes) == 0:
+            init_nodes = np.zeros(1, np.int32)
+        rc = load().mscd_run_init(self.h, gid, alphas.ctypes.data, len(alphas), seeds.ctypes.data, len(seeds),
+                                  init_ptr.ctypes.data, init_nodes.ctypes.data, 0, None)
+        if rc not in (OK, ETIMEOUT, EUNDECIDED):
+            raise MscdError(rc, load().mscd_last_error(self.h).decode() or "mscd_run_init")
+        self.n_scales = len(alphas)
+        self.n_seeds = len(seeds)
         return rc
 
     def membership(self, scale: int, seed_idx: int):

@@ -220,9 +220,30 @@ def config_graph(idx: int) -> CSRGraph:
         return hierarchical_lfr(1_000_000, 30, 300, 2.5, 1.5, (20, 1000), (0.3, 0.2, 0.1),
                                 weights=(0.5, 2.0), seed=2, name="lfr-1m-weighted")
     if idx == 4:
-        return hierarchical_lfr(2_000_000, 25, 250, 2.5, 1.5, (20, 1000), (0.3, 0.2, 0.1), seed=5,
-                                name="lfr-2m-serving")
+        return graph_from_spec(serving_specs()[0])
     raise ValueError(idx)
+
+
+def serving_specs(n_graphs=4, n=2_000_000, scale_nodes=1.0):
+    """The serving graphs: n nodes (times scale_nodes), mean degree 25, max 250,
+    three levels with mixing 0.3 / 0.2 / 0.1, unweighted; seeds 5, 6, ..."""
+    m = max(100, int(n * scale_nodes))
+    return [dict(n=m, mean_deg=25, max_deg=250, tau_deg=2.5, tau_size=1.5, size_range=(20, 1000),
+                 mixing=(0.3, 0.2, 0.1), seed=5 + i, name=f"lfr-2m-serving-{i}") for i in range(n_graphs)]
+
+
+def serving_queries(n_queries, graph_sizes, n_scales=16, max_seeds=4096, seed=7):
+    """Query stream: graph uniform, scale index uniform in [0, n_scales), seed
+    count uniform in {1..max_seeds}, seeds distinct and uniform over the graph."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(n_queries):
+        g = int(rng.integers(0, len(graph_sizes)))
+        s = int(rng.integers(0, n_scales))
+        k = int(rng.integers(1, max_seeds + 1))
+        seeds = rng.choice(graph_sizes[g], min(k, graph_sizes[g]), replace=False).astype(np.int32)
+        out.append((g, s, seeds))
+    return out
 
 
 def uneven_batch_specs(n_graphs=256, seed=4, n_range=(1_000, 200_000), scale_nodes=1.0):

@@ -273,3 +273,51 @@ def test_unit_order_independent(orc, ctx):
             i = perm[j]
             assert np.array_equal(nodes[ptr[j]:ptr[j + 1]], n0[p0[i]:p0[i + 1]])
     ctx.free_graph(gid)
+
+
+@pytest.mark.parametrize("small_class", [False, True])
+def test_initial_members_parity(orc, ctx, small_class):
+    """Growth from seeds plus initial members (repeats, the seed itself and
+    empty lists included) against the oracle; with a 32-slot first class the
+    larger initial sets overflow and are grown again in the next classes."""
+    from paper_1301_0955_gb300 import mscd
+
+    c = mscd.Context(0, smem_slots=32) if small_class else ctx
+    g = synth.config_graph(0)
+    G = oracle_graph(orc, g)
+    rng = np.random.default_rng(13 + small_class)
+    seeds = np.sort(rng.choice(g.n, 200, replace=False)).astype(np.int32)
+    lists = []
+    for i, sd in enumerate(seeds):
+        kind = i % 4
+        if kind == 0:
+            lists.append(np.zeros(0, np.int32))
+        elif kind == 1:  # a neighbourhood around the seed, with the seed and a repeat
+            nb = g.col[g.row_ptr[sd]:g.row_ptr[sd + 1]]
+            lists.append(np.concatenate([nb[:5], [sd], nb[:1]]).astype(np.int32))
+        else:  # random nodes anywhere
+            lists.append(rng.integers(0, g.n, int(rng.integers(1, 60 if kind == 2 else 300))).astype(np.int32))
+    iptr = np.concatenate([[0], np.cumsum([len(x) for x in lists])]).astype(np.int64)
+    inodes = np.concatenate(lists).astype(np.int32)
+    alphas = np.array([1.0, 0.7, 0.5])
+    gid = c.load_csr(g.n, g.row_ptr, g.col)
+    assert c.run_init(gid, alphas, seeds, iptr, inodes) == 0
+    rc, optr, onodes, of, ost = orc.run(G, alphas, seeds, threads=8, init=(iptr, inodes))
+    assert rc == 0
+    N = len(seeds)
+    for s in range(len(alphas)):
+        ptr, nodes, f, st = c.memberships(s)
+        op = optr[s * N:(s + 1) * N + 1] - optr[s * N]
+        assert np.array_equal(ptr, op) and np.array_equal(nodes, onodes[optr[s * N]:optr[(s + 1) * N]])
+        np.testing.assert_allclose(f, of[s * N:(s + 1) * N], rtol=F_RTOL, atol=0)
+        assert np.array_equal(st[:, :6], ost[s * N:(s + 1) * N, :6])
+    if small_class:
+        assert c.run_stats()["overflow_units"] > 0
+    with pytest.raises(mscd.MscdError) as e:  # a member id out of range
+        bad = inodes.copy()
+        bad[-1] = g.n
+        c.run_init(gid, alphas, seeds, iptr, bad)
+    assert e.value.rc == mscd.EINVAL
+    c.free_graph(gid)
+    if small_class:
+        c.close()

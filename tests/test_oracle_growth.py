@@ -233,3 +233,76 @@ def test_planted_recovery(orc):
         best_micro, best_macro = max(best_micro, jm), max(best_macro, jM)
     assert best_micro >= 0.9
     assert best_macro >= 0.9
+
+
+# ------------------------------------------------- growth from initial members
+
+def test_initial_members_empty_and_fixed_point(orc):
+    """Alg. 2 may start from given communities.  An empty initial set is the
+    plain growth; a grown community is a fixed point (no addition improves f,
+    so the first grow pass ends at once and no prune pass runs)."""
+    from paper_1301_0955_gb300 import synth
+
+    g = synth.config_graph(0)
+    G = orc.Graph(g.n, g.row_ptr, g.col)
+    seeds = np.arange(0, g.n, 7, dtype=np.int32)
+    alphas = [1.0, 0.6]
+    rc, ptr, nodes, f, st = orc.run(G, alphas, seeds, threads=4)
+    assert rc == 0
+    empty = (np.zeros(len(seeds) + 1, np.int64), np.zeros(0, np.int32))
+    rc, p0, n0, f0, st0 = orc.run(G, alphas, seeds, threads=4, init=empty)
+    assert rc == 0 and np.array_equal(p0, ptr) and np.array_equal(n0, nodes) and np.array_equal(st0, st)
+    N = len(seeds)
+    for s in range(2):
+        sl = ptr[s * N:(s + 1) * N + 1]
+        init = (sl - sl[0], nodes[sl[0]:sl[-1]])
+        rc, p1, n1, f1, st1 = orc.run(G, [alphas[s]], seeds, threads=4, init=init)
+        assert rc == 0
+        assert np.array_equal(p1, init[0]) and np.array_equal(n1, init[1])
+        assert (st1[:, 1] == 0).all() and (st1[:, 3] == 1).all() and (st1[:, 2] == 0).all()
+        np.testing.assert_array_equal(f1, f[s * N:(s + 1) * N])
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.5, 0.75])
+def test_initial_members_bruteforce(orc, alpha):
+    """From a random initial set on <= 12-node graphs: the seed stays; if a
+    node was added the result is a local optimum for single additions and
+    non-seed removals; if none was, the result is the initial set with the
+    seed and no single addition improves it."""
+    rng = random.Random(int(alpha * 77))
+    checked = 0
+    for it in range(50):
+        n = rng.randint(4, 12)
+        edges, w = random_small_graph(rng, n, rng.uniform(0.2, 0.6), it % 3 == 2)
+        if not edges:
+            continue
+        g, rp, col = graph_from_edges(orc, n, edges, w)
+        adj = [dict() for _ in range(n)]
+        for idx, (a, b) in enumerate(edges):
+            ww = 1 if w is None else w[idx]
+            adj[a][b] = ww
+            adj[b][a] = ww
+        k = [sum(adj[u].values()) for u in range(n)]
+        seeds = np.arange(n, dtype=np.int32)
+        inits = [rng.sample(range(n), rng.randint(0, n - 1)) for _ in range(n)]
+        iptr = np.concatenate([[0], np.cumsum([len(x) for x in inits])]).astype(np.int64)
+        inodes = np.array([v for x in inits for v in x], np.int32)
+        rc, ptr, nodes, f, st = orc.run(g, [alpha], seeds, init=(iptr, inodes))
+        assert rc == 0
+        for seed in range(n):
+            c = set(nodes[ptr[seed]:ptr[seed + 1]].tolist())
+            assert seed in c
+            K, V = kv(adj, k, c)
+            start = set(inits[seed]) | {seed}
+            if st[seed, 1] == 0:
+                assert c == start
+            for u in range(n):
+                if u in c:
+                    if u == seed or st[seed, 1] == 0:
+                        continue
+                    K2, V2 = kv(adj, k, c - {u})
+                else:
+                    K2, V2 = kv(adj, k, c | {u})
+                assert not f_greater(K2, V2, K, V, alpha), (edges, seed, sorted(c), u)
+            checked += 1
+    assert checked > 150
