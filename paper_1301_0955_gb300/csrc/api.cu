@@ -542,10 +542,10 @@ int run_impl(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
         // buffer; once the group is grown, each of its scales is deduplicated
         // and its units are pointed at their community's list (the lists are
         // equal), so the buffer is free again for the next group.  A group is
-        // as many scales as fit 40% of the free memory at the expected list
-        // length (1024 entries per unit at first, then twice the last group's
-        // mean); the persistent schedule usually needs one group, the plain
-        // form takes one scale at a time.
+        // as many scales as fit 35% of the free memory at the expected list
+        // length (1024 entries per unit, or twice the largest group mean seen:
+        // lists grow towards the coarse scales); the persistent schedule
+        // usually needs one group, the plain form takes one scale at a time.
         const bool per_scale = c->p.schedule == MSCD_SCHED_PER_SCALE;
         size_t free_mem = 0, total_mem = 0;
         cudaMemGetInfo(&free_mem, &total_mem);
@@ -590,7 +590,7 @@ int run_impl(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
         rc = grow_units(c->pipe, proto, group_units, ladder, in_smem, per_scale, out_budget, gr->max_part_n, &cursor);
         if (rc) break;
         if (group_units > 0)
-            per_unit = std::max(1.0, 2.0 * (double)cursor / (double)group_units);
+            per_unit = std::max(per_unit, 2.0 * (double)cursor / (double)group_units);
         if (!growth_only) {
             // dedup the group's scales; point their units at the community lists
             cudaEvent_t d0, d1;

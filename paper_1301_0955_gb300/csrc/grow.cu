@@ -232,19 +232,34 @@ __device__ __forceinline__ bool ranks_before(const S &st, int a, float ka, int b
     return swap ? !xfirst : xfirst;
 }
 
+// Warp-wide best of the lanes' candidates (slot `best`, key `bk`; -1 none),
+// returned to every lane.  The largest key comes from one integer max
+// reduction; only lanes within E2 of it can rank first, and when there are
+// several (rare) they are compared exactly in lane order.
 template <class S>
 __device__ __forceinline__ void warp_best(const S &st, int &best, float &bk, Unit &U) {
-#pragma unroll
-    for (int off = 16; off; off >>= 1) {
-        const int ob = __shfl_xor_sync(FULL_MASK, best, off);
-        const float ok = __shfl_xor_sync(FULL_MASK, bk, off);
-        if (ob >= 0 && (best < 0 || ranks_before(st, ob, ok, best, bk, U))) {
-            best = ob;
-            bk = ok;
+    const int om = __reduce_max_sync(FULL_MASK, best >= 0 ? ord(bk) : ORD_NEG_INF);
+    if (om == ORD_NEG_INF) {
+        best = -1;
+        bk = NEG_INF;
+        return;
+    }
+    const float mk = unord(om);
+    u32 cand = __ballot_sync(FULL_MASK, best >= 0 && !(mk - bk > U.E2));
+    int wb = -1;
+    float wk = NEG_INF;
+    while (cand) {
+        const int l = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const int b = __shfl_sync(FULL_MASK, best, l);
+        const float k = __shfl_sync(FULL_MASK, bk, l);
+        if (wb < 0 || ranks_before(st, b, k, wb, wk, U)) {
+            wb = b;
+            wk = k;
         }
     }
-    best = __shfl_sync(FULL_MASK, best, 0);
-    bk = __shfl_sync(FULL_MASK, bk, 0);
+    best = wb;
+    bk = wk;
 }
 
 constexpr int UNROLL = 4;
@@ -292,7 +307,7 @@ __device__ void rebuild_groups(const S &st, const Unit &U) {
         const float k = i < U.ns ? st.key[i] : NEG_INF;
         const int o = __reduce_max_sync(FULL_MASK, ord(k));
         const int q = __reduce_max_sync(
-            FULL_MASK, k == NEG_INF ? ORD_NEG_INF : ord((float)(i64)st.din[i] / (float)(i64)st.kdeg[i]));
+            FULL_MASK, k == NEG_INF ? ORD_NEG_INF : ord(__fdividef((float)(i64)st.din[i], (float)(i64)st.kdeg[i])));
         if (lane == 0) {
             st.gmax[g] = o;
             st.qmax[g] = q;
@@ -314,7 +329,10 @@ __device__ int queue_top(const S &st, Unit &U) {
     float bk = NEG_INF;
     int M = max_bound(st, G);
     for (int iter = 0; iter < 64; ++iter) {
-        if (M == ORD_NEG_INF) return best;
+        if (M == ORD_NEG_INF) {
+            warp_best(st, best, bk, U);
+            return best;
+        }
         const int othr = ord(unord(M) - 2.0f * U.E2);
         int mr = ORD_NEG_INF;  // largest refreshed (exact) bound
         for (int base = 0; base < G; base += 32) {
@@ -325,24 +343,28 @@ __device__ int queue_top(const S &st, Unit &U) {
                 ball &= ball - 1;
                 const int i = gg * 32 + lane;
                 const float k = i < U.ns ? st.key[i] : NEG_INF;
-                int lb = k == NEG_INF ? -1 : i;
-                float lk = k;
-                warp_best(st, lb, lk, U);
-                const int o = lb >= 0 ? ord(lk) : ORD_NEG_INF;
+                // the group's exact bound; candidates stay lane-local until the end
+                const int o = __reduce_max_sync(FULL_MASK, k == NEG_INF ? ORD_NEG_INF : ord(k));
                 if (lane == 0) st.gmax[gg] = o;
                 mr = max(mr, o);
-                if (lb >= 0 && (best < 0 || ranks_before(st, lb, lk, best, bk, U))) {
-                    best = lb;
-                    bk = lk;
+                if (k != NEG_INF && (best < 0 || ranks_before(st, i, k, best, bk, U))) {
+                    best = i;
+                    bk = k;
                 }
             }
         }
         __syncwarp();
         // every other bound is below othr <= M, so an unchanged maximum means done
-        if (mr == M) return best;
-        const int M2 = max_bound(st, G);
-        if (M2 == M) return best;
-        M = M2;
+        bool done = mr == M;
+        if (!done) {
+            const int M2 = max_bound(st, G);
+            done = M2 == M;
+            M = M2;
+        }
+        if (done) {
+            warp_best(st, best, bk, U);
+            return best;
+        }
     }
     return queue_top_flat(st, U);
 }
@@ -350,8 +372,9 @@ __device__ int queue_top(const S &st, Unit &U) {
 // Highest-ranked queued slot that passes the add test at the current K, V.
 // A node passes only if 2 d (V + k) > alpha K k (the filter below), so only if
 // d / k > alpha K / (2 (V + k_max)): groups whose d/k bound is below that are
-// skipped.  (The threshold and the d/k values carry a few roundings of 2^-24
-// each; the 2^-16 margin keeps the skip one-sided.)
+// skipped.  (The threshold and the d/k values carry errors of a few 2^-24
+// each, the quotients being the fast division within 2 ulp; the 2^-16 margin
+// keeps the skip one-sided.)
 template <class S>
 __device__ int best_passing(const S &st, Unit &U) {
     const int lane = threadIdx.x & 31;
@@ -439,7 +462,7 @@ __device__ void expand(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Uni
         }
         if (upd) {
             atomicMax(&st.gmax[s >> 5], ord(k));
-            atomicMax(&st.qmax[s >> 5], ord((float)(i64)st.din[s] / (float)(i64)st.kdeg[s]));
+            atomicMax(&st.qmax[s >> 5], ord(__fdividef((float)(i64)st.din[s], (float)(i64)st.kdeg[s])));
         }
     }
     __syncwarp();

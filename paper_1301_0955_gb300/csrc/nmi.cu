@@ -536,21 +536,44 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
             list = spill2;
         }
         if (nk > 0) {
+            // last tier: a global table per community, 2 min(incidences, |B|)
+            // entries; communities go in chunks whose tables fit a bounded
+            // scratch (a single table is at most 2^(1+ceil log2 |B|) entries)
             if ((rc = dev_alloc(&tsz, nk + 1, st))) break;
             if ((rc = dev_alloc(&toff, nk + 1, st))) break;
             spill_sizes<<<GB, 256, 0, st>>>(list, nk, active, A.comm_ptr, A.comm_nodes, MB.cnt, B.n_comms, tsz); note_launch();
-            if ((rc = scan_exclusive_i64(tsz, toff, nk, toff + nk, st))) break;
-            i64 TT = 0;
-            if ((rc = cuda_status(cudaMemcpyAsync(&TT, toff + nk, sizeof(i64), cudaMemcpyDeviceToHost, st)))) break;
+            std::vector<i64> hs(nk);
+            if ((rc = cuda_status(cudaMemcpyAsync(hs.data(), tsz, nk * sizeof(i64), cudaMemcpyDeviceToHost, st)))) break;
             if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
-            if ((rc = dev_alloc(&tkey, TT, st))) break;
-            if ((rc = dev_alloc(&tcnt, TT, st))) break;
-            if ((rc = cuda_status(cudaMemsetAsync(tkey, 0xff, TT * sizeof(i32), st)))) break;
-            if ((rc = cuda_status(cudaMemsetAsync(tcnt, 0, TT * sizeof(i32), st)))) break;
-            a.toff = toff;
+            i64 largest = 0;
+            for (i64 v : hs) largest = std::max(largest, v);
+            size_t fr = 0, tot = 0;
+            cudaMemGetInfo(&fr, &tot);
+            const i64 budget = std::max<i64>(largest, std::min<i64>((i64)1 << 28, (i64)(fr / 8 / (2 * sizeof(i32)))));
+            if ((rc = dev_alloc(&tkey, budget, st))) break;
+            if ((rc = dev_alloc(&tcnt, budget, st))) break;
             a.tkey = tkey;
             a.tcnt = tcnt;
-            pairs_global<<<GB, 256, 0, st>>>(a, list, nk); note_launch();
+            a.toff = toff;
+            std::vector<i64> ho;
+            for (i64 r0 = 0; r0 < nk && rc == MSCD_OK;) {
+                ho.assign(1, 0);
+                i64 r1 = r0;
+                while (r1 < nk && ho.back() + hs[r1] <= budget) {
+                    ho.push_back(ho.back() + hs[r1]);
+                    ++r1;
+                }
+                const i64 TT = ho.back();
+                if ((rc = cuda_status(cudaMemcpyAsync(toff, ho.data(), ho.size() * sizeof(i64), cudaMemcpyHostToDevice,
+                                                      st))))
+                    break;
+                if ((rc = cuda_status(cudaMemsetAsync(tkey, 0xff, TT * sizeof(i32), st)))) break;
+                if ((rc = cuda_status(cudaMemsetAsync(tcnt, 0, TT * sizeof(i32), st)))) break;
+                pairs_global<<<GB, 256, 0, st>>>(a, list + r0, r1 - r0); note_launch();
+                // the host offsets are read by the copy before the next chunk rewrites them
+                if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+                r0 = r1;
+            }
         }
         if (h[1] > 0) {
             disjoint_pairs<<<GB, 256, 0, st>>>(A.comm_ptr, A.comm_nodes, active, n_active, B.comm_ptr, B.comm_nodes,
