@@ -141,25 +141,6 @@ struct Unit {
     bool err;    // probe bound hit (cannot happen at load <= 1/2)
 };
 
-// Claim an empty bucket h for slot s (false if it was taken meanwhile).
-template <class HT>
-__device__ __forceinline__ bool claim_bucket(HT *hsh, u32 h, int s) {
-    if (sizeof(HT) == 4) return atomicCAS((u32 *)&hsh[h], 0u, (u32)(s + 1)) == 0u;
-    // 16-bit buckets: compare-and-swap on the aligned word holding the bucket
-    // (the bucket array is 4-byte aligned with an even length).  Each failure
-    // means one of the word's two buckets was filled, so it fails at most twice.
-    u32 *word = (u32 *)((uintptr_t)&hsh[h] & ~(uintptr_t)3);
-    const int sh = ((uintptr_t)&hsh[h] & 2) ? 16 : 0;
-    u32 old = *word;
-    for (int r = 0; r < 4; ++r) {
-        if ((old >> sh) & 0xffffu) return false;
-        const u32 got = atomicCAS(word, old, old | ((u32)(s + 1) << sh));
-        if (got == old) return true;
-        old = got;
-    }
-    return false;
-}
-
 // Look up (and insert if absent) node v for every active lane.  Warp-collective.
 template <class VT, class HT, bool WEIGHTED>
 __device__ int lookup_insert(const State<VT, HT, WEIGHTED> &st, const DevGraph &G, Unit &U, i32 v, bool active) {
@@ -199,13 +180,34 @@ __device__ int lookup_insert(const State<VT, HT, WEIGHTED> &st, const DevGraph &
             st.kdeg[slot] = (VT)G.k[v];
             st.key[slot] = NEG_INF;
             st.flag[slot] = 0;
-            int p = 0;
-            for (; p < st.H; ++p) {
-                if (claim_bucket(st.hsh, h, slot)) break;
-                h = (h + 1u) & hm;
-            }
-            if (p == st.H) U.err = true;
         }
+        // Claim the empty buckets found.  Only this warp writes its table, so
+        // lanes that found the same bucket are told apart with a match instead
+        // of atomics: the lowest takes it, the others move on to the next empty
+        // bucket; every round settles at least one lane.
+        const int lane = threadIdx.x & 31;
+        bool pending = need;
+        for (int r = 0; r <= 32; ++r) {
+            const u32 grp = __match_any_sync(FULL_MASK, pending ? h : 0xffffffffu - (u32)lane);
+            if (pending && __ffs(grp) - 1 == lane) {
+                st.hsh[h] = (HT)(slot + 1);
+                pending = false;
+            }
+            __syncwarp();
+            if (!__any_sync(FULL_MASK, pending)) break;
+            if (pending) {
+                int p = 0;
+                do {
+                    h = (h + 1u) & hm;
+                    ++p;
+                } while (st.hsh[h] != 0 && p < st.H);
+                if (p >= st.H) {
+                    U.err = true;
+                    pending = false;
+                }
+            }
+        }
+        if (pending) U.err = true;
         U.ns += cnt;
     }
     U.err = __any_sync(FULL_MASK, U.err);
@@ -433,11 +435,14 @@ __device__ void drop_before(const S &st, int best, Unit &U) {
 // their new key and fold them into their group's best.
 template <class VT, class HT, bool WEIGHTED>
 __device__ void expand(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Unit &U, int slot, int sign,
-                       bool requeue) {
+                       bool requeue, i64 rs = -1, i64 re = -1) {
     const DevGraph &G = a.G;
     const int lane = threadIdx.x & 31;
-    const i32 u = st.id[slot];
-    const i64 rs = G.rp[u], re = G.rp[u + 1];
+    if (rs < 0) {  // row bounds not loaded by the caller
+        const i32 u = st.id[slot];
+        rs = G.rp[u];
+        re = G.rp[u + 1];
+    }
     for (i64 b = rs; b < re; b += 32) {
         const i64 e = b + lane;
         const bool act = e < re;
@@ -472,7 +477,8 @@ __device__ void expand(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Uni
 // Add slot s to the community (an addition of the grow pass, or an initial
 // member, which is not counted as one).
 template <class VT, class HT, bool WEIGHTED>
-__device__ void accept(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Unit &U, int s, bool counted = true) {
+__device__ void accept(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Unit &U, int s, bool counted = true,
+                       i64 rs = -1, i64 re = -1) {
     const i64 d = st.din[s], kd = st.kdeg[s];
     __syncwarp();
     if ((threadIdx.x & 31) == 0) {
@@ -483,7 +489,7 @@ __device__ void accept(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Uni
     U.K += 2 * d;
     U.V += kd;
     if (counted) U.adds++;
-    expand(st, a, U, s, +1, true);
+    expand(st, a, U, s, +1, true, rs, re);
 }
 
 // Smallest-id member (not the seed, id > last) whose removal raises f; -1 if none.
@@ -685,14 +691,18 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
             const int top = queue_top(st, U);
             if (top < 0) break;
             int s = top;
+            // the row of the likely addition, loading during the test
+            const i32 utop = st.id[top];
+            i64 rs = G.rp[utop], re = G.rp[utop + 1];
             if (!exact::add_test(U.K, U.V, (i64)st.din[top], (i64)st.kdeg[top], U.alpha, U.alpha32, &U.xflags)) {
                 s = best_passing(st, U);
                 // none passes: every queued node is popped and rejected, the grow
                 // pass ends (the next round rebuilds every key)
                 if (s < 0) break;
                 drop_before(st, s, U);
+                rs = -1;
             }
-            accept(st, a, U, s);
+            accept(st, a, U, s, true, rs, re);
             added++;
             if (U.ovf || U.err) break;
         }
