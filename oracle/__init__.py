@@ -37,6 +37,13 @@ def lib():
         L.orc_run_init.argtypes = [C.c_void_p, f64p, C.c_int32, i32p, C.c_int64, i64p, i32p, C.c_int64, C.c_int,
                                    C.POINTER(C.c_void_p)]
         L.orc_result_destroy.argtypes = [C.c_void_p]
+        L.orc_full.argtypes = [C.c_void_p, f64p, C.c_int32, C.c_int, i32p, i64p, i32p, C.c_int64, C.c_double,
+                               C.c_int64, C.POINTER(C.c_void_p)]
+        L.orc_full_destroy.argtypes = [C.c_void_p]
+        L.orc_full_sizes.argtypes = [C.c_void_p, C.c_int32, i64p, i64p, i64p, i64p]
+        L.orc_full_get.argtypes = [C.c_void_p, C.c_int32, i64p, i32p, i32p, f64p]
+        L.orc_full_n_seeds.argtypes = [C.c_void_p, i32p]
+        L.orc_full_n_seeds.restype = C.c_int64
         L.orc_result_sizes.argtypes = [C.c_void_p, i64p]
         L.orc_result_get.argtypes = [C.c_void_p, i64p, i32p, f64p, i64p]
         L.orc_sign_delta.argtypes = [C.c_int64] * 4 + [C.c_double, C.POINTER(C.c_int)]
@@ -211,3 +218,43 @@ def unique_communities(ptr, nodes):
     for c, u in enumerate(first):
         cnodes[cptr[c]:cptr[c + 1]] = nodes[ptr[u]:ptr[u + 1]]
     return cptr, cnodes, u2c, first
+
+
+def full(g: Graph, alphas, seed_rule=1, prio=None, init=None, eta=0.5, max_iters=1000):
+    """The full method of Alg. 2 (seed rules, growth with the overlap pre-test,
+    check and merge, carried over from scale to scale).  prio: int32[n] order
+    of the seed candidates (lower first); init: optional (ptr, nodes) initial
+    communities.  Returns (status, initial seeds, [per scale dict(ptr, nodes,
+    seeds, f, iterations, merges)])."""
+    alphas = np.ascontiguousarray(alphas, np.float64)
+    h = C.c_void_p()
+    if init is None:
+        prio = np.ascontiguousarray(prio if prio is not None else np.arange(g.n), np.int32)
+        rc = lib().orc_full(g.h, _p(alphas, f64p), len(alphas), int(seed_rule), _p(prio, i32p), None, None, 0,
+                            float(eta), int(max_iters), C.byref(h))
+    else:
+        iptr = np.ascontiguousarray(init[0], np.int64)
+        inodes = np.ascontiguousarray(init[1], np.int32)
+        dummy = np.zeros(1, np.int32)
+        rc = lib().orc_full(g.h, _p(alphas, f64p), len(alphas), 0, _p(dummy, i32p), _p(iptr, i64p),
+                            _p(inodes if len(inodes) else dummy, i32p), len(iptr) - 1, float(eta), int(max_iters),
+                            C.byref(h))
+    if not h.value:
+        return rc, None, None
+    ns = lib().orc_full_n_seeds(h, None)
+    seeds0 = np.zeros(max(ns, 1), np.int32)
+    lib().orc_full_n_seeds(h, _p(seeds0, i32p))
+    out = []
+    for s in range(len(alphas)):
+        nc, nn, it, mg = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        if lib().orc_full_sizes(h, s, C.byref(nc), C.byref(nn), C.byref(it), C.byref(mg)) != 0:
+            break
+        ptr = np.zeros(nc.value + 1, np.int64)
+        nodes = np.zeros(max(nn.value, 1), np.int32)
+        sd = np.zeros(max(nc.value, 1), np.int32)
+        f = np.zeros(max(nc.value, 1), np.float64)
+        lib().orc_full_get(h, s, _p(ptr, i64p), _p(nodes, i32p), _p(sd, i32p), _p(f, f64p))
+        out.append(dict(ptr=ptr, nodes=nodes[:nn.value], seeds=sd[:nc.value], f=f[:nc.value],
+                        iterations=it.value, merges=mg.value))
+    lib().orc_full_destroy(h)
+    return rc, seeds0[:ns], out

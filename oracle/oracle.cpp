@@ -393,7 +393,7 @@ struct Grower {
 // communities is given"; the seed stays pinned, repeats are ignored, the
 // insertions are not counted as additions).
 static void grow_unit(const orc_graph &g, i32 seed, double alpha, i64 max_rounds, UnitResult &R,
-                      const i32 *init = nullptr, i64 n_init = 0) {
+                      const i32 *init = nullptr, i64 n_init = 0, bool single = false) {
     Grower gr{g, alpha};
     std::unordered_map<i32, i64> din;  // d_in(u, c) for every node touched
     std::unordered_map<i32, char> inC;  // membership
@@ -476,6 +476,7 @@ static void grow_unit(const orc_graph &g, i32 seed, double alpha, i64 max_rounds
             }
             if (removed == 0) break;
         }
+        if (single) break;  // one grow call of Alg. 1 (the full method repeats it itself)
     }
     R.rounds = rounds;
     for (auto &kv : inC)
@@ -755,4 +756,243 @@ extern "C" int orc_scales_logspaced(double vmin, double a, i32 x, double *out) {
     double lx = std::log((double)x);
     for (i32 k = 1; k <= x; k++) out[k - 1] = vmin + (a - vmin) * (1.0 - std::log((double)k) / lx);
     return ORC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The full method of Alg. 2 (with the modified growth of Alg. 3), written out
+// sequentially in a fixed order:
+//   * seeds (no initial communities given): candidates are the nodes with at
+//     least two neighbours, taken in increasing `prio` (the random order of
+//     the paper, passed in); a candidate still available becomes a seed and
+//     makes its neighbours (rule 1) and also their neighbours (rule 2)
+//     unavailable.  Community i starts as {seed_i}.  Given initial
+//     communities, each is taken as it is, its first listed node as its seed.
+//   * for every scale, while changes can be made:
+//       - membership sets of the current communities;
+//       - each community, in index order, against those sets: if it shares
+//         at least eta * min(|c|, |c'|) nodes with another community c' it
+//         is put on the check list unchanged (Alg. 3 pre-test); otherwise it
+//         is grown once by Alg. 1 (grow pass, then prune passes if it added)
+//         from its current members, its seed kept, and put on the check list
+//         if its member set changed;
+//       - membership sets again; every community on the check list, in index
+//         order, counts shared nodes over its members in ascending id and,
+//         for each member, over that node's communities in ascending index;
+//         the first other community whose count reaches the threshold forms
+//         a pair (c, c') to merge;
+//       - merge rounds: the pairs are taken in list order into a round when
+//         neither community is in the round yet; each taken pair merges c'
+//         into c (union, c keeps its seed); in the remaining pairs c' is
+//         renamed c and pairs that became (c, c) are dropped; repeat;
+//       - a change is a grown community whose set changed or a merge.
+//   * the communities left at the end of a scale (index order) are its
+//     result and the start of the next scale.
+// Merge criterion (Sec. 3): max(|A n B| / |A|, |A n B| / |B|) >= eta.
+// ---------------------------------------------------------------------------
+
+struct orc_full_result {
+    std::vector<std::vector<std::vector<i32>>> comms;  // [scale][community] sorted members
+    std::vector<std::vector<i32>> seeds;               // [scale][community]
+    std::vector<std::vector<double>> f;                // [scale][community]
+    std::vector<i64> iterations, merges, grown;        // [scale]
+    std::vector<i32> initial_seeds;
+};
+
+static bool reaches(i64 count, i64 a, i64 b, double eta) { return (double)count >= eta * (double)std::min(a, b); }
+
+// First community (other than c) whose shared-node count with c reaches the
+// threshold in the scan order described above; -1 if none.
+static i64 first_reaching(const std::vector<std::vector<i32>> &C, const std::vector<char> &alive,
+                          const std::vector<std::vector<i64>> &memsets, i64 c, double eta) {
+    std::unordered_map<i64, i64> count;
+    for (i32 n : C[c])
+        for (i64 o : memsets[n]) {
+            if (o == c || !alive[o]) continue;
+            i64 &k = ++count[o];
+            if (reaches(k, (i64)C[c].size(), (i64)C[o].size(), eta)) return o;
+        }
+    return -1;
+}
+
+extern "C" int orc_full(const orc_graph *g, const double *alphas, i32 n_scales, int seed_rule, const i32 *prio,
+                        const i64 *init_ptr, const i32 *init_nodes, i64 n_init, double eta, i64 max_iters,
+                        orc_full_result **out) {
+    *out = nullptr;
+    if (n_scales < 1 || !(eta > 0.0) || eta > 1.0) return ORC_EINVAL;
+    for (i32 s = 0; s < n_scales; s++)
+        if (!(alphas[s] > 0.0) || !std::isfinite(alphas[s])) return ORC_EINVAL;
+    const i64 n = g->n;
+    std::vector<std::vector<i32>> C;
+    std::vector<i32> seed;
+    if (init_ptr) {
+        for (i64 i = 0; i < n_init; i++) {
+            std::vector<i32> m(init_nodes + init_ptr[i], init_nodes + init_ptr[i + 1]);
+            if (m.empty()) return ORC_EINVAL;
+            for (i32 v : m)
+                if (v < 0 || v >= n) return ORC_EINVAL;
+            seed.push_back(m[0]);
+            std::sort(m.begin(), m.end());
+            m.erase(std::unique(m.begin(), m.end()), m.end());
+            C.push_back(m);
+        }
+    } else {
+        if (seed_rule != 1 && seed_rule != 2) return ORC_EINVAL;
+        std::vector<i32> order(n);
+        for (i64 u = 0; u < n; u++) order[u] = (i32)u;
+        std::sort(order.begin(), order.end(), [&](i32 a, i32 b) { return prio[a] < prio[b] || (prio[a] == prio[b] && a < b); });
+        std::vector<char> avail(n, 0);
+        for (i64 u = 0; u < n; u++) avail[u] = (g->rp[u + 1] - g->rp[u]) >= 2;
+        for (i32 u : order) {
+            if (!avail[u]) continue;
+            seed.push_back(u);
+            C.push_back({u});
+            avail[u] = 0;
+            for (i64 e = g->rp[u]; e < g->rp[u + 1]; e++) {
+                const i32 v = g->col[e];
+                avail[v] = 0;
+                if (seed_rule == 2)
+                    for (i64 f = g->rp[v]; f < g->rp[v + 1]; f++) avail[g->col[f]] = 0;
+            }
+        }
+    }
+    orc_full_result *r = new orc_full_result();
+    r->initial_seeds = seed;
+    int status = ORC_OK;
+    for (i32 sc = 0; sc < n_scales; sc++) {
+        const double alpha = alphas[sc];
+        std::vector<char> alive(C.size(), 1);
+        i64 it = 0, merges = 0, grown = 0;
+        for (;; it++) {
+            if (it >= max_iters) { status = ORC_ETIMEOUT; break; }
+            auto build = [&](std::vector<std::vector<i64>> &ms) {
+                ms.assign(n, {});
+                for (i64 c = 0; c < (i64)C.size(); c++)
+                    if (alive[c])
+                        for (i32 v : C[c]) ms[v].push_back(c);
+            };
+            std::vector<std::vector<i64>> memsets;
+            build(memsets);
+            std::vector<char> check(C.size(), 0);
+            bool changes = false;
+            std::vector<std::vector<i32>> next = C;
+            for (i64 c = 0; c < (i64)C.size(); c++) {
+                if (!alive[c]) continue;
+                if (first_reaching(C, alive, memsets, c, eta) >= 0) {
+                    check[c] = 1;
+                    continue;
+                }
+                UnitResult R;
+                grow_unit(*g, seed[c], alpha, 1000000, R, C[c].data(), (i64)C[c].size(), true);
+                if (R.status == ORC_EUNDECIDED) status = ORC_EUNDECIDED;
+                grown++;
+                if (R.members != C[c]) {
+                    next[c] = R.members;
+                    check[c] = 1;
+                    changes = true;
+                }
+            }
+            C.swap(next);
+            build(memsets);
+            std::vector<std::pair<i64, i64>> pairs;
+            for (i64 c = 0; c < (i64)C.size(); c++)
+                if (alive[c] && check[c]) {
+                    const i64 o = first_reaching(C, alive, memsets, c, eta);
+                    if (o >= 0) pairs.push_back({c, o});
+                }
+            while (!pairs.empty()) {
+                std::vector<char> used(C.size(), 0);
+                std::vector<std::pair<i64, i64>> round, rest;
+                for (auto &pq : pairs) {
+                    if (pq.first != pq.second && !used[pq.first] && !used[pq.second]) {
+                        used[pq.first] = used[pq.second] = 1;
+                        round.push_back(pq);
+                    } else {
+                        rest.push_back(pq);
+                    }
+                }
+                std::vector<i64> into(C.size());
+                for (i64 c = 0; c < (i64)C.size(); c++) into[c] = c;
+                for (auto &pq : round) {
+                    std::vector<i32> u;
+                    std::set_union(C[pq.first].begin(), C[pq.first].end(), C[pq.second].begin(), C[pq.second].end(),
+                                   std::back_inserter(u));
+                    C[pq.first].swap(u);
+                    C[pq.second].clear();
+                    alive[pq.second] = 0;
+                    into[pq.second] = pq.first;
+                    merges++;
+                    changes = true;
+                }
+                pairs.clear();
+                for (auto &pq : rest) {
+                    const i64 a = into[pq.first], b = into[pq.second];
+                    if (a != b) pairs.push_back({a, b});
+                }
+            }
+            if (!changes) break;
+        }
+        // compact: the communities left, in index order
+        std::vector<std::vector<i32>> keep;
+        std::vector<i32> kseed;
+        for (i64 c = 0; c < (i64)C.size(); c++)
+            if (alive[c]) {
+                keep.push_back(C[c]);
+                kseed.push_back(seed[c]);
+            }
+        C.swap(keep);
+        seed.swap(kseed);
+        std::vector<double> fs;
+        for (auto &m : C) {
+            i64 K = 0, V = 0;
+            std::unordered_map<i32, char> in;
+            for (i32 v : m) in[v] = 1;
+            for (i32 v : m) {
+                V += g->k[v];
+                for (i64 e = g->rp[v]; e < g->rp[v + 1]; e++)
+                    if (in.count(g->col[e])) K += g->wt(e);
+            }
+            fs.push_back(fitness(K, V, alpha, g->unit_exp));
+        }
+        r->comms.push_back(C);
+        r->seeds.push_back(seed);
+        r->f.push_back(fs);
+        r->iterations.push_back(it);
+        r->merges.push_back(merges);
+        r->grown.push_back(grown);
+        if (status == ORC_ETIMEOUT) break;
+    }
+    *out = r;
+    return status;
+}
+
+extern "C" void orc_full_destroy(orc_full_result *r) { delete r; }
+
+// Sizes of scale s: communities, member entries.
+extern "C" int orc_full_sizes(const orc_full_result *r, i32 s, i64 *n_comms, i64 *n_nodes, i64 *iters, i64 *merges) {
+    if (s < 0 || s >= (i32)r->comms.size()) return ORC_EINVAL;
+    *n_comms = (i64)r->comms[s].size();
+    i64 t = 0;
+    for (auto &m : r->comms[s]) t += (i64)m.size();
+    *n_nodes = t;
+    if (iters) *iters = r->iterations[s];
+    if (merges) *merges = r->merges[s];
+    return ORC_OK;
+}
+
+extern "C" int orc_full_get(const orc_full_result *r, i32 s, i64 *ptr, i32 *nodes, i32 *seeds, double *f) {
+    if (s < 0 || s >= (i32)r->comms.size()) return ORC_EINVAL;
+    ptr[0] = 0;
+    for (size_t c = 0; c < r->comms[s].size(); c++) {
+        const auto &m = r->comms[s][c];
+        std::copy(m.begin(), m.end(), nodes + ptr[c]);
+        ptr[c + 1] = ptr[c] + (i64)m.size();
+        if (seeds) seeds[c] = r->seeds[s][c];
+        if (f) f[c] = r->f[s][c];
+    }
+    return ORC_OK;
+}
+
+extern "C" i64 orc_full_n_seeds(const orc_full_result *r, i32 *seeds) {
+    if (seeds) std::copy(r->initial_seeds.begin(), r->initial_seeds.end(), seeds);
+    return (i64)r->initial_seeds.size();
 }
