@@ -96,7 +96,9 @@ typedef struct mscd_params {
                                 one launch per scale and slot class, one unit per warp,
                                 statically mapped (no persistence, no work stealing); the
                                 results are identical, only the speed differs           */
-    int32_t reserved;        /* 0                                                        */
+    int32_t hash_smem_slots; /* global-arena classes of at most this many slots keep
+                                their hash table (and group bounds) in shared memory,
+                                the slot arrays in the arena (0 = none)               */
 } mscd_params;
 
 #define MSCD_SCHED_PERSISTENT 0
@@ -305,6 +307,48 @@ int mscd_grow_noalloc(mscd_ctx *ctx, int32_t graph_id, const double *alphas, int
                       const int32_t *seeds, int64_t n_seeds, int32_t *out_nodes, int64_t out_cap,
                       int64_t *out_offset, int32_t *out_len, double *out_fitness, int64_t *out_stats,
                       int32_t *out_status, uint64_t *out_hash, int64_t *n_nodes_needed, void *cuda_stream);
+
+/* ------------------------------------------------------------- full method
+ * The paper's whole algorithm (Alg. 2 with the growth of Alg. 3) rather than
+ * one independent community per (scale, seed): seeds chosen by rule 1 (a
+ * seed's neighbours cannot be seeds) or rule 2 (nor their neighbours) from the
+ * nodes with at least two neighbours, taken in the order `prio` gives (the
+ * paper's random order, passed in: int32[n], lower first, ties by id); or
+ * given initial communities (init_ptr int64[n_init+1] from 0, init_nodes; the
+ * first listed node of each is its seed).  For every scale in the given
+ * order, while changes can be made: every community is grown once by Alg. 1
+ * from its current members (seed kept) unless it already shares at least
+ * eta * min(|c|, |c'|) nodes with another community c'; grown communities that
+ * changed and the flagged ones are checked, each finding its first such
+ * partner in the scan order of Alg. 2 (members ascending); the pairs merge in
+ * rounds of disjoint pairs (the partner joins the checked community, which
+ * keeps its seed).  The communities at the end of a scale start the next.
+ * Every step is deterministic (see the design notes for the order taken).
+ * Host pointers.  ETIMEOUT: a scale needed more than max_iters iterations. */
+typedef struct mscd_full_params {
+    int32_t struct_size;  /* sizeof(mscd_full_params)                          */
+    int32_t seed_rule;    /* 1 or 2 (0 = 1)                                    */
+    double eta;           /* merge ratio in (0, 1] (0 = 0.5, Sec. 3's default) */
+    int64_t max_iters;    /* iterations per scale before ETIMEOUT (0 = 1000)   */
+} mscd_full_params;
+
+int mscd_full_run(mscd_ctx *ctx, int32_t graph_id, const double *alphas, int32_t n_scales, const int32_t *prio,
+                  const int64_t *init_ptr, const int32_t *init_nodes, int64_t n_init,
+                  const mscd_full_params *params, void *cuda_stream);
+
+/* Seeds of the last full run, in the order they were chosen. */
+int mscd_full_get_seeds(mscd_ctx *ctx, int32_t *seeds, int64_t cap, int64_t *n);
+
+/* Communities at the end of scale `scale`: ptr int64[n_comms+1], nodes int32
+ * (each list ascending), seeds int32[n_comms] and fitness double[n_comms]
+ * (either may be NULL).  ESMALL with the sizes when a buffer is short. */
+int mscd_full_get_scale(mscd_ctx *ctx, int32_t scale, int64_t *ptr, int64_t ptr_cap, int32_t *nodes,
+                        int64_t nodes_cap, int32_t *seeds, double *fitness, int64_t *n_comms, int64_t *n_nodes);
+
+/* Iterations of the while loop, merges and growth calls at a scale, and the
+ * overlapping NMI (Sec. 4) between its communities and the next scale's. */
+int mscd_full_get_info(mscd_ctx *ctx, int32_t scale, int64_t *iterations, int64_t *merges, int64_t *grown,
+                       double *nmi_next);
 
 /* ------------------------------------------------------------------ serving
  * Local-community queries answered as they arrive (no counterpart in the

@@ -108,6 +108,11 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 struct Server;
 void serve_destroy(Server *s);
+struct FullState;
+void full_state_free(FullState *f);
+int full_run(const DevGraph &G, i64 max_part_n, const double *alphas, int32_t n_scales, int seed_rule,
+             const i32 *prio_host, const i64 *init_ptr, const i32 *init_nodes, i64 n_init, double eta,
+             i64 max_iters, GrowPipe &pipe, FullState *out, cudaStream_t st);
 bool serve_graph_busy(Server *s, int32_t graph_id);
 
 struct mscd_ctx {
@@ -139,6 +144,7 @@ struct mscd_ctx {
     // the growth pipeline of runs: its arena, retry lists and output buffer are reused
     GrowPipe pipe;
     Server *server = nullptr;  // query serving (mscd_serve_start)
+    FullState *full = nullptr;  // last run of the full method (mscd_full_run)
     char last_error[160] = "";  // where the last failed run stopped
 };
 
@@ -219,6 +225,15 @@ bool ctx_graph(mscd_ctx *c, int32_t graph_id, DevGraph *g, int *device) {
 }
 
 Server **ctx_server(mscd_ctx *c) { return &c->server; }
+FullState **ctx_full(mscd_ctx *c) { return &c->full; }
+
+GrowPipe *ctx_pipe(mscd_ctx *c, cudaStream_t st) {
+    c->pipe.p = c->p;
+    c->pipe.p.schedule = MSCD_SCHED_PERSISTENT;
+    c->pipe.st = st ? st : c->own;
+    c->pipe.stats = nullptr;
+    return &c->pipe;
+}
 
 bool ctx_graph_part(mscd_ctx *c, int32_t id, DevGraph *g, i64 *max_part_n) {
     GraphRec *r = find_graph(c, id);
@@ -301,6 +316,8 @@ int mscd_destroy(mscd_ctx *c) {
     if (!c) return MSCD_EINVAL;
     serve_destroy(c->server);
     c->server = nullptr;
+    full_state_free(c->full);
+    c->full = nullptr;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->own);
     free_run(c);

@@ -215,11 +215,17 @@ __device__ __forceinline__ int sign_delta(i64 a1, i64 a2, i64 b1, i64 b2, double
 // three times, <= 1 ulp from log1pf / logf), alpha32 = fl(alpha) adds
 // u32 alpha |L2|, the fused multiply-add one more rounding; the sign is taken
 // when |Delta| > 2^-18 (|L1| + alpha |L2|) = 64 u32 (...).
+// int64 -> binary32, rounded to nearest.  Values that fit 32 bits take the
+// 32-bit conversion (same result; the 64-bit one is a slow instruction here).
+__device__ __forceinline__ float i2f(i64 x) {
+    return x == (i64)(int)x ? __int2float_rn((int)x) : __ll2float_rn(x);
+}
+
 __device__ __forceinline__ float log_ratio32(i64 a1, i64 a2) {
     i64 diff = a1 - a2;
     u64 ad = diff < 0 ? (u64)(-diff) : (u64)diff;
-    if (ad <= (u64)a2 / 2) return log1pf((float)diff / (float)a2);
-    return logf((float)a1 / (float)a2);
+    if (ad <= (u64)a2 / 2) return log1pf(i2f(diff) / i2f(a2));
+    return logf(i2f(a1) / i2f(a2));
 }
 
 __device__ __forceinline__ int sign_delta32(i64 a1, i64 a2, i64 b1, i64 b2, double alpha, float alpha32,
@@ -253,13 +259,13 @@ __device__ __forceinline__ bool remove_test(i64 K, i64 V, i64 d, i64 k, double a
 // carries at most ~6 roundings of 2^-24 (alpha32 included), so a 2^-19
 // margin keeps the filters one-sided.
 __device__ __forceinline__ bool add_possible(i64 K, i64 V, i64 d, i64 k, float alpha32) {
-    float lhs = 2.0f * (float)d * (float)(V + k);  // V + k formed exactly in int64
-    float rhs = alpha32 * (float)K * (float)k;
+    float lhs = 2.0f * i2f(d) * i2f(V + k);  // V + k formed exactly in int64
+    float rhs = alpha32 * i2f(K) * i2f(k);
     return lhs > rhs * (1.0f - 0x1p-19f);
 }
 __device__ __forceinline__ bool remove_possible(i64 K, i64 V, i64 d, i64 k, float alpha32) {
-    float lhs = 2.0f * (float)d * (float)(V - k);  // no cancellation: V - k exact in int64
-    float rhs = alpha32 * (float)K * (float)k;
+    float lhs = 2.0f * i2f(d) * i2f(V - k);  // no cancellation: V - k exact in int64
+    float rhs = alpha32 * i2f(K) * i2f(k);
     return lhs < rhs * (1.0f + 0x1p-19f);
 }
 

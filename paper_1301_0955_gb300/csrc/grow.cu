@@ -85,7 +85,7 @@ __host__ __device__ __forceinline__ size_t state_bytes_t(int C) {
 }
 
 template <class VT, class HT, bool WEIGHTED>
-__device__ __forceinline__ State<VT, HT, WEIGHTED> carve(unsigned char *base, int C, int *bounds) {
+__device__ __forceinline__ State<VT, HT, WEIGHTED> carve(unsigned char *base, int C, int *bounds, HT *hsh) {
     State<VT, HT, WEIGHTED> s;
     s.C = C;
     s.H = 2 * C;
@@ -106,7 +106,7 @@ __device__ __forceinline__ State<VT, HT, WEIGHTED> carve(unsigned char *base, in
         s.gmax = bounds;
         s.qmax = bounds + C / 32;
     }
-    s.hsh = (HT *)(base + o);
+    s.hsh = hsh ? hsh : (HT *)(base + o);  // the table may live in shared memory
     o += 2 * sizeof(HT) * (size_t)C;
     s.flag = base + o;
     return s;
@@ -216,7 +216,7 @@ __device__ int lookup_insert(const State<VT, HT, WEIGHTED> &st, const DevGraph &
 }
 
 __device__ __forceinline__ float rank_key(i64 d, i64 k, float alpha32) {
-    return logf((float)d) - alpha32 * logf((float)k);
+    return logf(exact::i2f(d)) - alpha32 * logf(exact::i2f(k));
 }
 
 // Slot a ranks before slot b (exact; canonical argument order so that every
@@ -309,7 +309,8 @@ __device__ void rebuild_groups(const S &st, const Unit &U) {
         const float k = i < U.ns ? st.key[i] : NEG_INF;
         const int o = __reduce_max_sync(FULL_MASK, ord(k));
         const int q = __reduce_max_sync(
-            FULL_MASK, k == NEG_INF ? ORD_NEG_INF : ord(__fdividef((float)(i64)st.din[i], (float)(i64)st.kdeg[i])));
+            FULL_MASK,
+            k == NEG_INF ? ORD_NEG_INF : ord(__fdividef(exact::i2f((i64)st.din[i]), exact::i2f((i64)st.kdeg[i]))));
         if (lane == 0) {
             st.gmax[g] = o;
             st.qmax[g] = q;
@@ -381,7 +382,7 @@ template <class S>
 __device__ int best_passing(const S &st, Unit &U) {
     const int lane = threadIdx.x & 31;
     const int G = (U.ns + 31) >> 5;
-    const float tau = U.alpha32 * (float)U.K / (2.0f * ((float)U.V + U.kmaxf)) * (1.0f - 0x1p-16f);
+    const float tau = U.alpha32 * exact::i2f(U.K) / (2.0f * (exact::i2f(U.V) + U.kmaxf)) * (1.0f - 0x1p-16f);
     const int otau = ord(tau);
     int best = -1;
     float bk = NEG_INF;
@@ -467,7 +468,7 @@ __device__ void expand(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Uni
         }
         if (upd) {
             atomicMax(&st.gmax[s >> 5], ord(k));
-            atomicMax(&st.qmax[s >> 5], ord(__fdividef((float)(i64)st.din[s], (float)(i64)st.kdeg[s])));
+            atomicMax(&st.qmax[s >> 5], ord(__fdividef(exact::i2f((i64)st.din[s]), exact::i2f((i64)st.kdeg[s]))));
         }
     }
     __syncwarp();
@@ -720,6 +721,7 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
             }
             if (removed == 0 || U.ovf || U.err) break;
         }
+        if (a.single_round) break;
     }
     U.xflags = __reduce_or_sync(FULL_MASK, U.xflags);
     if (U.err) {
@@ -748,8 +750,11 @@ __global__ void __launch_bounds__(MAXT, MINB) grow_kernel(GrowArgs a) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const i64 gw = (i64)blockIdx.x * (blockDim.x >> 5) + wib;
     unsigned char *base = a.use_smem ? smem + (size_t)wib * a.state_bytes : a.gstate + (size_t)gw * a.state_bytes;
-    int *bounds = a.bounds_smem ? (int *)smem + (size_t)wib * 2 * (a.cap / 32) : nullptr;
-    const State<VT, HT, WEIGHTED> st = carve<VT, HT, WEIGHTED>(base, a.cap, bounds);
+    // global-arena classes: group bounds and hash table of the warp in shared memory if asked
+    unsigned char *wsm = smem + (size_t)wib * a.smem_per_warp;
+    int *bounds = a.bounds_smem ? (int *)wsm : nullptr;
+    HT *hsh = a.hash_smem ? (HT *)(wsm + (a.bounds_smem ? 8 * (size_t)(a.cap / 32) : 0)) : nullptr;
+    const State<VT, HT, WEIGHTED> st = carve<VT, HT, WEIGHTED>(base, a.cap, bounds, hsh);
     for (int i = lane; i < st.H; i += 32) st.hsh[i] = 0;
     __syncwarp();
     // one call site of grow_unit, and nothing of the plain form live across it
@@ -790,7 +795,7 @@ int launch_k(const GrowArgs &a, int blocks, int threads, size_t smem, cudaStream
 #endif
 template <class VT, class HT, bool WEIGHTED>
 int launch_t(const GrowArgs &a, int blocks, int threads, size_t smem, cudaStream_t st, int *occ) {
-    if (a.use_smem) return launch_k<VT, HT, WEIGHTED, GROW_MAX_THREADS, 1>(a, blocks, threads, smem, st, occ);
+    if (a.use_smem || a.hash_smem) return launch_k<VT, HT, WEIGHTED, GROW_MAX_THREADS, 1>(a, blocks, threads, smem, st, occ);
     return launch_k<VT, HT, WEIGHTED, GLOBAL_CTA_THREADS, GLOBAL_MIN_BLOCKS>(a, blocks, threads, smem, st, occ);
 }
 

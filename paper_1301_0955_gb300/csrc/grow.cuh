@@ -17,6 +17,7 @@ struct GrowArgs {
     // optional initial members per seed index (init_ptr[si]..init_ptr[si+1])
     const i64 *init_ptr;
     const i32 *init_nodes;
+    int single_round;       // one grow call of Alg. 1 (the full method repeats it itself)
     // work: units 0..n_work-1, or the listed units
     const i64 *work_list;
     i64 n_work;
@@ -29,6 +30,8 @@ struct GrowArgs {
     int cap;                // node slots per unit (power of 2, >= 32)
     int use_smem;           // 1: dynamic shared memory, 0: global arena
     int bounds_smem;        // global arena with the group bounds in dynamic shared memory
+    int hash_smem;          // ... and the hash table too (after the bounds)
+    size_t smem_per_warp;   // dynamic shared memory of one warp in a global-arena class
     unsigned char *big_seed;  // per seed: outgrew this class at a finer scale (first class only; may be null)
     unsigned char *gstate;  // global arena (warps * state_bytes)
     size_t state_bytes;     // per warp

@@ -176,15 +176,28 @@ int grow_units(GrowPipe &w, const GrowArgs &proto, i64 n_units, const std::vecto
         } else {
             a.use_smem = 0;
             a.bounds_smem = 0;
-            const int wpc = GLOBAL_CTA_THREADS / 32;
-            // group bounds (8 bytes per 32 slots and unit) in shared memory when small
-            if (cap <= 16384) {
+            a.hash_smem = 0;
+            int wpc = GLOBAL_CTA_THREADS / 32;
+            i64 per_sm_warps = w.p.global_warps_per_sm;
+            const size_t hash_bytes = 2 * (size_t)cap * (cap <= 32768 ? 2 : 4);
+            const size_t bounds_bytes = 8 * (size_t)(cap / 32);
+            if (cap <= w.p.hash_smem_slots) {
+                // hash table and bounds in shared memory, slot arrays in the arena:
+                // as many warps per CTA (one CTA per SM) as their tables fit
                 a.bounds_smem = 1;
-                smem = (size_t)wpc * 8 * (size_t)(cap / 32);
+                a.hash_smem = 1;
+                a.smem_per_warp = (bounds_bytes + hash_bytes + 15) & ~(size_t)15;
+                wpc = (int)std::max<size_t>(1, std::min<size_t>(16, (220 * 1024) / a.smem_per_warp));
+                smem = (size_t)wpc * a.smem_per_warp;
+                per_sm_warps = wpc;
+            } else if (cap <= 16384) {
+                // group bounds (8 bytes per 32 slots and unit) in shared memory when small
+                a.bounds_smem = 1;
+                a.smem_per_warp = bounds_bytes;
+                smem = (size_t)wpc * a.smem_per_warp;
             }
             const size_t budget = (size_t)4 << 30;
-            i64 warps = std::max<i64>(
-                1, std::min<i64>((i64)(budget / a.state_bytes), (i64)w.sm_count * w.p.global_warps_per_sm));
+            i64 warps = std::max<i64>(1, std::min<i64>((i64)(budget / a.state_bytes), (i64)w.sm_count * per_sm_warps));
             if (plain) warps = (i64)(budget / a.state_bytes);
             warps = std::max<i64>(1, std::min<i64>(warps, std::max<i64>(n_work, 1)));
             if (plain) chunk = warps;

@@ -38,7 +38,7 @@ class mscd_params(C.Structure):
     _fields_ = [("struct_size", C.c_int32), ("warps_per_block", C.c_int32), ("smem_slots", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("mid_slots", C.c_int32), ("global_warps_per_sm", C.c_int32),
                 ("global_slots", C.c_int32), ("max_rounds", C.c_int64), ("schedule", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("hash_smem_slots", C.c_int32)]
 
 
 class mscd_serve_params(C.Structure):
@@ -49,6 +49,10 @@ class mscd_serve_params(C.Structure):
 class mscd_serve_stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("queries_submitted", "queries_done", "units_done", "batches", "queued",
                                          "in_flight_bytes", "max_in_flight_bytes", "budget_bytes")]
+
+
+class mscd_full_params(C.Structure):
+    _fields_ = [("struct_size", C.c_int32), ("seed_rule", C.c_int32), ("eta", C.c_double), ("max_iters", C.c_int64)]
 
 
 class mscd_run_stats(C.Structure):
@@ -87,6 +91,11 @@ SIGNATURES = {
     "mscd_get_stability": (C.c_int, [vp, f64p, f64p, f64p]),
     "mscd_get_stability_part": (C.c_int, [vp, C.c_int32, f64p, f64p, f64p]),
     "mscd_autotune": (C.c_int, [vp, C.c_int32, f64p, C.c_int32, C.c_int64, C.c_uint32, C.POINTER(mscd_params), f64p]),
+    "mscd_full_run": (C.c_int, [vp, C.c_int32, f64p, C.c_int32, i32p, i64p, i32p, C.c_int64,
+                                C.POINTER(mscd_full_params), vp]),
+    "mscd_full_get_seeds": (C.c_int, [vp, i32p, C.c_int64, i64p]),
+    "mscd_full_get_scale": (C.c_int, [vp, C.c_int32, i64p, C.c_int64, i32p, C.c_int64, i32p, f64p, i64p, i64p]),
+    "mscd_full_get_info": (C.c_int, [vp, C.c_int32, i64p, i64p, i64p, f64p]),
     "mscd_serve_start": (C.c_int, [vp, C.POINTER(mscd_serve_params)]),
     "mscd_serve_stop": (C.c_int, [vp]),
     "mscd_query_submit": (C.c_int, [vp, C.c_int32, i32p, C.c_int32, C.c_double, C.POINTER(C.c_uint64)]),
@@ -159,10 +168,10 @@ class Context:
 
     def __init__(self, device: int = 0, smem_slots: int = 0, blocks_per_sm: int = 0, max_rounds: int = 0,
                  warps_per_block: int = 0, mid_slots: int = 0, global_warps_per_sm: int = 0,
-                 global_slots: int = 0, schedule: int = 0):
+                 global_slots: int = 0, schedule: int = 0, hash_smem_slots: int = 0):
         L = load()
         p = mscd_params(C.sizeof(mscd_params), warps_per_block, smem_slots, blocks_per_sm, mid_slots,
-                        global_warps_per_sm, global_slots, max_rounds, schedule, 0)
+                        global_warps_per_sm, global_slots, max_rounds, schedule, hash_smem_slots)
         h = vp()
         _check(L.mscd_create(C.byref(h), device, C.byref(p)), "mscd_create")
         self.h = h
@@ -211,6 +220,57 @@ class Context:
         _check(load().mscd_autotune(self.h, gid, alphas.ctypes.data_as(f64p), len(alphas), n_sample, flags,
                                     C.byref(p), C.byref(ms)), "mscd_autotune")
         return {k: getattr(p, k) for k, _ in mscd_params._fields_}, ms.value
+
+    # ---- the full method (Alg. 2)
+    def full_run(self, gid: int, alphas, prio=None, init=None, seed_rule: int = 1, eta: float = 0.5,
+                 max_iters: int = 0) -> int:
+        alphas = np.ascontiguousarray(alphas, np.float64)
+        p = mscd_full_params(C.sizeof(mscd_full_params), seed_rule, eta, max_iters)
+        if init is None:
+            n = self.graph_info(gid)["n"]
+            prio = np.ascontiguousarray(prio if prio is not None else np.arange(n), np.int32)
+            rc = load().mscd_full_run(self.h, gid, alphas.ctypes.data_as(f64p), len(alphas),
+                                      prio.ctypes.data_as(i32p), None, None, 0, C.byref(p), None)
+        else:
+            iptr = np.ascontiguousarray(init[0], np.int64)
+            inodes = np.ascontiguousarray(init[1], np.int32)
+            rc = load().mscd_full_run(self.h, gid, alphas.ctypes.data_as(f64p), len(alphas), None,
+                                      iptr.ctypes.data_as(i64p), inodes.ctypes.data_as(i32p), len(iptr) - 1,
+                                      C.byref(p), None)
+        if rc not in (OK, ETIMEOUT, EUNDECIDED):
+            raise MscdError(rc, "mscd_full_run")
+        self.full_scales = len(alphas)
+        return rc
+
+    def full_seeds(self) -> np.ndarray:
+        n = C.c_int64()
+        rc = load().mscd_full_get_seeds(self.h, None, 0, C.byref(n))
+        if rc not in (OK, ESMALL):
+            _check(rc, "mscd_full_get_seeds")
+        out = np.zeros(max(n.value, 1), np.int32)
+        _check(load().mscd_full_get_seeds(self.h, out.ctypes.data_as(i32p), len(out), C.byref(n)),
+               "mscd_full_get_seeds")
+        return out[: n.value]
+
+    def full_scale(self, s: int) -> dict:
+        L = load()
+        nc, nn = C.c_int64(), C.c_int64()
+        rc = L.mscd_full_get_scale(self.h, s, None, 0, None, 0, None, None, C.byref(nc), C.byref(nn))
+        if rc not in (OK, ESMALL):
+            _check(rc, "mscd_full_get_scale")
+        ptr = np.zeros(nc.value + 1, np.int64)
+        nodes = np.zeros(max(nn.value, 1), np.int32)
+        seeds = np.zeros(max(nc.value, 1), np.int32)
+        f = np.zeros(max(nc.value, 1), np.float64)
+        _check(L.mscd_full_get_scale(self.h, s, ptr.ctypes.data_as(i64p), len(ptr), nodes.ctypes.data_as(i32p),
+                                     len(nodes), seeds.ctypes.data_as(i32p), f.ctypes.data_as(f64p), C.byref(nc),
+                                     C.byref(nn)), "mscd_full_get_scale")
+        it, mg, gr = C.c_int64(), C.c_int64(), C.c_int64()
+        nmi = C.c_double()
+        _check(L.mscd_full_get_info(self.h, s, C.byref(it), C.byref(mg), C.byref(gr), C.byref(nmi)),
+               "mscd_full_get_info")
+        return dict(ptr=ptr, nodes=nodes[: nn.value], seeds=seeds[: nc.value], f=f[: nc.value],
+                    iterations=it.value, merges=mg.value, grown=gr.value, nmi_next=nmi.value)
 
     # ---- serving
     def serve_start(self, workers: int = 0, max_batch_units: int = 0, memory_budget: int = 0):

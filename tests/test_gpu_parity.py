@@ -168,15 +168,16 @@ def test_planted_full_parity(orc, ctx):
 
 
 @pytest.mark.parametrize("weighted", [False, True])
-@pytest.mark.parametrize("schedule", [0, 1])
-def test_slot_class_escalation(orc, ctx, weighted, schedule):
+@pytest.mark.parametrize("schedule,hybrid", [(0, False), (1, False), (0, True)])
+def test_slot_class_escalation(orc, ctx, weighted, schedule, hybrid):
     """Tiny shared-memory classes force units through every class: two
     shared-memory classes, then global arenas of growing capacity, in the
-    persistent schedule and in the plain one-launch-per-scale form.  Results
+    persistent schedule and in the plain one-launch-per-scale form, and with
+    the first global class keeping its hash table in shared memory.  Results
     must not change."""
     from paper_1301_0955_gb300 import mscd
 
-    c2 = mscd.Context(0, smem_slots=32, mid_slots=64, schedule=schedule)
+    c2 = mscd.Context(0, smem_slots=32, mid_slots=64, schedule=schedule, hash_smem_slots=512 if hybrid else 0)
     g = synth.config_graph(0)
     w = None
     if weighted:
