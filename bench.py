@@ -59,7 +59,8 @@ def parse_args():
     p.add_argument("--flush-mib", type=int, default=1024, help="L2 flush buffer written between steps")
     p.add_argument("--plain-steps", type=int, default=1,
                    help="steps of the plain one-launch-per-scale form timed for comparison (0: skip)")
-    p.add_argument("--workload", default="lfr-100k", choices=["lfr-100k", "uneven-batch", "serve"])
+    p.add_argument("--workload", default="lfr-100k", choices=["lfr-100k", "uneven-batch", "serve", "full"])
+    p.add_argument("--full-rule", type=int, default=1, help="full: seed rule 1 or 2")
     p.add_argument("--serve-queries", type=int, default=10000, help="serve: queries per load level")
     p.add_argument("--serve-calibration", type=int, default=1000, help="serve: queries of the saturation run")
     p.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95])
@@ -394,6 +395,78 @@ def serve_phase(ctx, gids, alphas, queries, rate_qps):
     return {"latency_ms": lat, "queue_ms": queued, "wall_s": wall, "units": units}
 
 
+def run_full(args):
+    """The full method (Alg. 2): seeds by rule 1 in a seeded random order,
+    carry-over across the 20 scales of the lfr-100k workload, growth, check
+    and merge until nothing changes at each scale."""
+    from paper_1301_0955_gb300 import build, mscd, synth
+
+    world, rank, local = dist_env()
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    L = mscd.load()
+    g = synth.config_graph(1)
+    alphas = mscd.scales_logspaced(0.5, 1.0, N_SCALES)
+    prio = np.random.default_rng(11).permutation(g.n).astype(np.int32)
+    ctx = mscd.Context(local)
+    gid = ctx.load_csr(g.n, g.row_ptr, g.col)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        assert ctx.full_run(gid, alphas, prio=prio, seed_rule=args.full_rule) == mscd.OK
+
+    for _ in range(args.warmup):
+        step()
+    times = []
+    l0 = L.mscd_launch_count()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            step()
+            torch.cuda.synchronize(dev)
+            times.append((time.perf_counter() - t0) * 1e3)
+    launches = L.mscd_launch_count() - l0
+    info = [ctx.full_scale(s) for s in range(N_SCALES)]
+    grown = sum(i["grown"] for i in info)
+    ms = statistics.mean(times)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        G = oracle.Graph(g.n, g.row_ptr, g.col)
+        # a bounded sample: the first scales only, until about cpu_seconds pass
+        # a bounded sample: the first k scales, k doubling until one run takes
+        # about half the budget
+        k, dt = 1, 0.0
+        while True:
+            t0 = time.perf_counter()
+            rc, seeds, out = oracle.full(G, alphas[:k], args.full_rule, prio)
+            dt = time.perf_counter() - t0
+            if dt >= args.cpu_seconds / 2 or k >= N_SCALES:
+                break
+            k = min(N_SCALES, 2 * k)
+        gpu_k = sum(info[s]["grown"] for s in range(k))
+        cpu = {"kind": "oracle", "cores": 1, "sample": "the oracle's full method on the same graph and seeds, "
+               "the first %d scales, %.1f s" % (k, dt), "value": gpu_k / max(dt, 1e-9),
+               "unit": "growth calls/s", "ms_for_these_scales": dt * 1e3}
+    line = {"metric": "full method (Alg. 2) run time", "value": ms, "unit": "ms per run", "higher_is_better": False,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": "int64+f64",
+            "config": {"workload": WORKLOAD.replace("every node a seed", "seed rule %d in a seeded random order, "
+                                                    "eta 0.5" % args.full_rule)},
+            "growth_calls": grown, "growth_calls_per_s": grown / (ms / 1e3),
+            "seeds": int(len(ctx.full_seeds())),
+            "communities_per_scale": [int(len(i["ptr"]) - 1) for i in info],
+            "iterations_per_scale": [i["iterations"] for i in info],
+            "merges_per_scale": [i["merges"] for i in info],
+            "cpu_baseline": cpu, "clocks": clk.summary(), "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_serve(args):
     """Serving: resident graphs, a Poisson stream of local-community queries,
     continuous batching; p50/p99 latency at fractions of saturation."""
@@ -548,6 +621,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "full":
+        run_full(args)
         return
     world, rank, local = dist_env()
     wl = WORKLOADS[args.workload](args)  # host-side generation before the first GPU call
