@@ -59,7 +59,8 @@ def parse_args():
     p.add_argument("--flush-mib", type=int, default=1024, help="L2 flush buffer written between steps")
     p.add_argument("--plain-steps", type=int, default=1,
                    help="steps of the plain one-launch-per-scale form timed for comparison (0: skip)")
-    p.add_argument("--workload", default="lfr-100k", choices=["lfr-100k", "uneven-batch", "serve", "full"])
+    p.add_argument("--workload", default="lfr-100k", choices=["lfr-100k", "uneven-batch", "serve", "full", "accuracy"])
+    p.add_argument("--acc-scales", type=int, default=40, help="accuracy: scales in [0.3, 1]")
     p.add_argument("--full-rule", type=int, default=1, help="full: seed rule 1 or 2")
     p.add_argument("--serve-queries", type=int, default=10000, help="serve: queries per load level")
     p.add_argument("--serve-calibration", type=int, default=1000, help="serve: queries of the saturation run")
@@ -467,6 +468,84 @@ def run_full(args):
     ctx.close()
 
 
+ACC_SETTINGS = [(0.05, 0.2), (0.05, 0.3), (0.2, 0.4), (0.3, 0.4)]  # (macro mu1, micro mu2), Table 1
+
+
+def planted_cover(labels):
+    order = np.argsort(labels, kind="stable").astype(np.int32)
+    counts = np.bincount(labels)
+    ptr = np.concatenate([[0], np.cumsum(counts[counts > 0])]).astype(np.int64)
+    return ptr, order
+
+
+def scale_ranges(alphas, vals, thr):
+    """Scale intervals (in the list's order) where vals >= thr."""
+    out, cur = [], None
+    for a, v in zip(alphas, vals):
+        if v >= thr:
+            cur = [a, a] if cur is None else [cur[0], a]
+        elif cur is not None:
+            out.append(cur)
+            cur = None
+    if cur is not None:
+        out.append(cur)
+    return [[round(min(r), 3), round(max(r), 3)] for r in out]
+
+
+def run_accuracy(args):
+    """The shape of the paper's Table 1: at which scales the macro and micro
+    communities of two-level LFR-style graphs (n = 10^4, m ~ 10^5) are found,
+    for the four mixing settings, by the full method (seed rules 1 and 2) and
+    by the independent growth of every seed with dedup."""
+    from paper_1301_0955_gb300 import build, mscd, synth
+
+    world, rank, local = dist_env()
+    import torch
+
+    torch.cuda.set_device(local)
+    build.build()
+    alphas = mscd.scales_logspaced(0.3, 1.0, args.acc_scales)
+    ctx = mscd.Context(local)
+    rows = []
+    t_start = time.perf_counter()
+    for i, (mu1, mu2) in enumerate(ACC_SETTINGS):
+        g = synth.hierarchical_lfr(10_000, 30, 100, 2.0, 1.0, (10, 50), (mu2, mu1), group_range=(2, 6),
+                                   seed=200 + i, name="acc-%d" % i)
+        gid = ctx.load_csr(g.n, g.row_ptr, g.col)
+        planted = [planted_cover(g.labels[1]), planted_cover(g.labels[0])]  # macro, micro
+        prio = np.random.default_rng(300 + i).permutation(g.n).astype(np.int32)
+        for method in ("full rule 1", "full rule 2", "every seed + dedup"):
+            covers = []
+            if method.startswith("full"):
+                ctx.full_run(gid, alphas, prio=prio, seed_rule=1 if method.endswith("1") else 2)
+                for s in range(len(alphas)):
+                    r = ctx.full_scale(s)
+                    covers.append((r["ptr"], r["nodes"]))
+            else:
+                ctx.run(gid, alphas)
+                for s in range(len(alphas)):
+                    ptr, nodes, f, s2c = ctx.communities(s)
+                    covers.append((ptr, nodes))
+            res = {"mu1": mu1, "mu2": mu2, "method": method}
+            for lvl, name in ((0, "macro"), (1, "micro")):
+                nm = [ctx.nmi_covers(g.n, c, planted[lvl]) for c in covers]
+                b = int(np.nanargmax(nm))
+                res[name] = {"best_nmi": round(float(nm[b]), 4), "at_scale": round(float(alphas[b]), 4),
+                             "scales_nmi_ge_0.9": scale_ranges(alphas, nm, 0.9),
+                             "scales_nmi_ge_0.5": scale_ranges(alphas, nm, 0.5)}
+            rows.append(res)
+        ctx.free_graph(gid)
+    line = {"metric": "scale ranges where planted macro / micro communities are found (Table 1 shape)",
+            "value": None, "unit": "scale intervals", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "4 two-level LFR-style graphs, n=10^4, m ~ 9.5*10^4 (degree power law 2, "
+                                   "max 100), micro "
+                                   "communities 10-50 nodes grouped 2-6 per macro community, (mu1 macro, mu2 "
+                                   "micro) in %s; %d log-spaced scales in [0.3, 1]" % (ACC_SETTINGS, len(alphas))},
+            "rows": rows, "seconds": time.perf_counter() - t_start}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_serve(args):
     """Serving: resident graphs, a Poisson stream of local-community queries,
     continuous batching; p50/p99 latency at fractions of saturation."""
@@ -624,6 +703,9 @@ def main():
         return
     if args.workload == "full":
         run_full(args)
+        return
+    if args.workload == "accuracy":
+        run_accuracy(args)
         return
     world, rank, local = dist_env()
     wl = WORKLOADS[args.workload](args)  # host-side generation before the first GPU call

@@ -272,6 +272,13 @@ int mscd_get_stability_part(mscd_ctx *ctx, int32_t part, double *nmi_succ, doubl
 /* Totals of the last run. */
 int mscd_get_run_stats(mscd_ctx *ctx, mscd_run_stats *out);
 
+/* The overlapping NMI of Sec. 4 between two covers of n nodes given on the
+ * host (ptr int64[n_x+1], nodes int32: each list non-empty, strictly
+ * ascending, ids in [0, n); EINVAL otherwise), e.g. a scale's communities
+ * against a reference partition.  NaN if a cover is empty. */
+int mscd_nmi_covers(mscd_ctx *ctx, int64_t n, const int64_t *ptr_a, const int32_t *nodes_a, int64_t n_a,
+                    const int64_t *ptr_b, const int32_t *nodes_b, int64_t n_b, double *nmi);
+
 /* Where the last failed mscd_run stopped and why ("" if none failed), e.g.
  * "mscd_run: dedup of scale 3: device memory allocation failed".  The string
  * belongs to the context and stays valid until its next failed run. */

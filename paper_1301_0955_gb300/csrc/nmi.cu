@@ -42,6 +42,8 @@
 #include "common.cuh"
 #include "dedup.cuh"
 
+int ctx_device_of(mscd_ctx *c);
+
 namespace {
 
 constexpr int NMI_WARPS = 8;
@@ -684,4 +686,70 @@ int nmi_between(const ScaleResult &X, const ScaleResult &Y, i64 n, const i64 *pa
     cudaFreeAsync(cnt, st);
     cudaFreeAsync(acc, st);
     return rc != MSCD_OK ? rc : cuda_status(cudaGetLastError());
+}
+
+// ---- NMI between two covers given by the caller -------------------------
+
+namespace {
+
+__device__ __forceinline__ u64 mix_list(u64 x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return x;
+}
+
+// Warp per community: a hash of its sorted list (equal lists, equal hashes).
+__global__ void list_hashes(const i64 *ptr, const i32 *nodes, i64 C, u64 *hash) {
+    const int lane = threadIdx.x & 31;
+    const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
+    for (i64 c = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < C; c += warps) {
+        const i64 n = ptr[c + 1] - ptr[c];
+        u64 h = 0;
+        for (i64 i = lane; i < n; i += 32) h += mix_list((u64)(u32)nodes[ptr[c] + i] + 0x9E3779B97F4A7C15ull * (u64)(i + 1));
+        for (int o = 16; o; o >>= 1) h += __shfl_xor_sync(FULL_MASK, h, o);
+        if (lane == 0) {
+            h ^= mix_list((u64)n);
+            hash[c] = h ? h : 1;
+        }
+    }
+}
+
+// Copy a host cover (each list sorted, no repeats, ids in [0, n)) to the device.
+int cover_to_device(const int64_t *ptr, const int32_t *nodes, int64_t C, i64 n, ScaleResult *R, cudaStream_t st) {
+    R->n_comms = C;
+    R->n_nodes = ptr[C];
+    for (int64_t c = 0; c < C; ++c) {
+        if (ptr[c + 1] <= ptr[c]) return MSCD_EINVAL;
+        for (int64_t e = ptr[c]; e < ptr[c + 1]; ++e)
+            if (nodes[e] < 0 || nodes[e] >= n || (e > ptr[c] && nodes[e] <= nodes[e - 1])) return MSCD_EINVAL;
+    }
+    MSCD_CUDA(cudaMalloc((void **)&R->comm_ptr, (C + 1) * sizeof(i64)));
+    MSCD_CUDA(cudaMalloc((void **)&R->comm_nodes, std::max<i64>(R->n_nodes, 1) * sizeof(i32)));
+    MSCD_CUDA(cudaMalloc((void **)&R->comm_hash, std::max<i64>(C, 1) * sizeof(u64)));
+    MSCD_CUDA(cudaMemcpyAsync(R->comm_ptr, ptr, (C + 1) * sizeof(i64), cudaMemcpyHostToDevice, st));
+    if (R->n_nodes > 0)
+        MSCD_CUDA(cudaMemcpyAsync(R->comm_nodes, nodes, R->n_nodes * sizeof(i32), cudaMemcpyHostToDevice, st));
+    if (C > 0) { list_hashes<<<GB, 256, 0, st>>>(R->comm_ptr, R->comm_nodes, C, R->comm_hash); note_launch(); }
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" int mscd_nmi_covers(mscd_ctx *ctx, int64_t n, const int64_t *ptr_a, const int32_t *nodes_a, int64_t n_a,
+                               const int64_t *ptr_b, const int32_t *nodes_b, int64_t n_b, double *nmi) {
+    if (!ctx || n < 1 || !ptr_a || !ptr_b || !nmi || n_a < 0 || n_b < 0) return MSCD_EINVAL;
+    if ((ptr_a[n_a] > 0 && !nodes_a) || (ptr_b[n_b] > 0 && !nodes_b)) return MSCD_EINVAL;
+    MSCD_CUDA(cudaSetDevice(ctx_device_of(ctx)));
+    cudaStream_t st = nullptr;
+    ScaleResult A, B;
+    int rc = cover_to_device(ptr_a, nodes_a, n_a, n, &A, st);
+    if (!rc) rc = cover_to_device(ptr_b, nodes_b, n_b, n, &B, st);
+    if (!rc) rc = nmi_between(A, B, n, nullptr, 1, nmi, st);
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+    scale_result_free(&A);
+    scale_result_free(&B);
+    return rc;
 }

@@ -107,6 +107,7 @@ SIGNATURES = {
     "mscd_graph_parts": (C.c_int, [vp, C.c_int32, i64p, C.c_int32, i32p]),
     "mscd_get_run_stats": (C.c_int, [vp, C.POINTER(mscd_run_stats)]),
     "mscd_last_error": (C.c_char_p, [vp]),
+    "mscd_nmi_covers": (C.c_int, [vp, C.c_int64, i64p, i32p, C.c_int64, i64p, i32p, C.c_int64, f64p]),
     "mscd_grow_noalloc": (C.c_int, [vp, C.c_int32, f64p, C.c_int32, vp, C.c_int64, vp, C.c_int64, vp, vp, vp, vp,
                                     vp, vp, i64p, vp]),
 }
@@ -220,6 +221,16 @@ class Context:
         _check(load().mscd_autotune(self.h, gid, alphas.ctypes.data_as(f64p), len(alphas), n_sample, flags,
                                     C.byref(p), C.byref(ms)), "mscd_autotune")
         return {k: getattr(p, k) for k, _ in mscd_params._fields_}, ms.value
+
+    def nmi_covers(self, n: int, a, b) -> float:
+        """Overlapping NMI between covers a, b = (ptr, nodes) of n nodes."""
+        pa, na = np.ascontiguousarray(a[0], np.int64), np.ascontiguousarray(a[1], np.int32)
+        pb, nb = np.ascontiguousarray(b[0], np.int64), np.ascontiguousarray(b[1], np.int32)
+        out = C.c_double()
+        _check(load().mscd_nmi_covers(self.h, n, pa.ctypes.data_as(i64p), na.ctypes.data_as(i32p), len(pa) - 1,
+                                      pb.ctypes.data_as(i64p), nb.ctypes.data_as(i32p), len(pb) - 1, C.byref(out)),
+               "mscd_nmi_covers")
+        return out.value
 
     # ---- the full method (Alg. 2)
     def full_run(self, gid: int, alphas, prio=None, init=None, seed_rule: int = 1, eta: float = 0.5,
