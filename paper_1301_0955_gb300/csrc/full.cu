@@ -635,7 +635,7 @@ int full_run(const DevGraph &G, i64 max_part_n, const double *alphas, int32_t n_
             std::vector<unsigned char> changed(std::max<i64>(m, 1), 0);
             if (m > 0) {
                 // one grow call from the current members of each unflagged community
-                i32 *dlist = nullptr, *dseeds = nullptr, *iseed = nullptr, *dunit = nullptr, *ulen = nullptr,
+                i32 *dlist = nullptr, *dseeds = nullptr, *dunit = nullptr, *ulen = nullptr,
                     *ustatus = nullptr;
                 i64 *ilen = nullptr, *iptr = nullptr, *uoff = nullptr, *ustat = nullptr, *nlen = nullptr,
                     *nptr = nullptr;

@@ -197,20 +197,25 @@ struct DirArgs {
 
 // Warp per active A community: intersections with every B community it meets
 // (shared-memory hash), minimum admitted candidate.
+// The buckets a community fills are listed as they are claimed, so the scan
+// and the reset after it touch only those (the table is cleared once).
 __global__ void __launch_bounds__(NMI_WARPS * 32) pairs_smem(DirArgs a) {
     __shared__ i32 skey[NMI_WARPS][NMI_TABLE];
     __shared__ i32 scnt[NMI_WARPS][NMI_TABLE];
+    __shared__ unsigned short sused[NMI_WARPS][NMI_TABLE / 2];
     __shared__ int sfill[NMI_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const i64 warps = (i64)gridDim.x * NMI_WARPS;
     i32 *keys = skey[w];
     i32 *cnts = scnt[w];
+    unsigned short *used = sused[w];
+    for (int t = lane; t < NMI_TABLE; t += 32) {
+        keys[t] = -1;
+        cnts[t] = 0;
+    }
+    __syncwarp();
     for (i64 q = (i64)blockIdx.x * NMI_WARPS + w; q < a.n_active; q += warps) {
         const i32 k = a.active[q];
-        for (int t = lane; t < NMI_TABLE; t += 32) {
-            keys[t] = -1;
-            cnts[t] = 0;
-        }
         if (lane == 0) sfill[w] = 0;
         __syncwarp();
         bool over = false;
@@ -224,7 +229,9 @@ __global__ void __launch_bounds__(NMI_WARPS * 32) pairs_smem(DirArgs a) {
                     if (cur == -1) {
                         cur = atomicCAS(&keys[h], -1, l);
                         if (cur == -1) {
-                            if (atomicAdd(&sfill[w], 1) >= NMI_TABLE / 2) over = true;
+                            const int f = atomicAdd(&sfill[w], 1);
+                            if (f >= NMI_TABLE / 2) over = true;
+                            else used[f] = (unsigned short)h;
                             cur = l;
                         }
                     }
@@ -237,18 +244,26 @@ __global__ void __launch_bounds__(NMI_WARPS * 32) pairs_smem(DirArgs a) {
             }
             over = __any_sync(FULL_MASK, over);
         }
+        __syncwarp();
         if (over) {
             if (lane == 0) a.spill[atomicAdd(a.n_spill, 1ull)] = q;
+            for (int t = lane; t < NMI_TABLE; t += 32) {  // more buckets than listed: clear all
+                keys[t] = -1;
+                cnts[t] = 0;
+            }
             __syncwarp();
             continue;
         }
-        __syncwarp();
+        const int nf = sfill[w];
         const i64 sa = a.aptr[k + 1] - a.aptr[k], n = a.acn[k];
         const double inv_n = 1.0 / (double)n;
         double bx = __longlong_as_double((long long)a.best[k]);
-        for (int t = lane; t < NMI_TABLE; t += 32) {
-            const i32 l = keys[t];
-            if (l >= 0) bx = min(bx, cond_candidate(cnts[t], sa, a.bptr[l + 1] - a.bptr[l], n, inv_n));
+        for (int t = lane; t < nf; t += 32) {
+            const int h = used[t];
+            const i32 l = keys[h];
+            bx = min(bx, cond_candidate(cnts[h], sa, a.bptr[l + 1] - a.bptr[l], n, inv_n));
+            keys[h] = -1;
+            cnts[h] = 0;
         }
         for (int o = 16; o; o >>= 1) bx = min(bx, __shfl_xor_sync(FULL_MASK, bx, o));
         if (lane == 0) a.best[k] = min_bits(bx);
@@ -308,16 +323,17 @@ __global__ void __launch_bounds__(BLK_WARPS * 32) pairs_block(DirArgs a, const i
                                                               unsigned long long *n_spill2) {
     extern __shared__ i32 tab[];
     i32 *keys = tab, *cnts = tab + BLK_TABLE;
+    unsigned short *used = (unsigned short *)(tab + 2 * BLK_TABLE);  // [BLK_TABLE / 2]
     __shared__ int fill, over;
     __shared__ double wmin[BLK_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < BLK_TABLE; t += BLK_WARPS * 32) {
+        keys[t] = -1;
+        cnts[t] = 0;
+    }
     for (i64 r = blockIdx.x; r < nk; r += gridDim.x) {
         const i64 q = list[r];
         const i32 k = a.active[q];
-        for (int t = threadIdx.x; t < BLK_TABLE; t += BLK_WARPS * 32) {
-            keys[t] = -1;
-            cnts[t] = 0;
-        }
         if (threadIdx.x == 0) {
             fill = 0;
             over = 0;
@@ -334,7 +350,9 @@ __global__ void __launch_bounds__(BLK_WARPS * 32) pairs_block(DirArgs a, const i
                     if (cur == -1) {
                         cur = atomicCAS(&keys[h], -1, l);
                         if (cur == -1) {
-                            if (atomicAdd(&fill, 1) >= BLK_TABLE / 2) over = 1;
+                            const int f = atomicAdd(&fill, 1);
+                            if (f >= BLK_TABLE / 2) over = 1;
+                            else used[f] = (unsigned short)h;
                             cur = l;
                         }
                     }
@@ -349,15 +367,23 @@ __global__ void __launch_bounds__(BLK_WARPS * 32) pairs_block(DirArgs a, const i
         __syncthreads();
         if (over) {
             if (threadIdx.x == 0) spill2[atomicAdd(n_spill2, 1ull)] = q;
+            for (int t = threadIdx.x; t < BLK_TABLE; t += BLK_WARPS * 32) {  // clear all
+                keys[t] = -1;
+                cnts[t] = 0;
+            }
             __syncthreads();
             continue;
         }
+        const int nf = fill;
         const i64 sa = a.aptr[k + 1] - a.aptr[k], n = a.acn[k];
         const double inv_n = 1.0 / (double)n;
         double bx = __builtin_huge_val();
-        for (int t = threadIdx.x; t < BLK_TABLE; t += BLK_WARPS * 32) {
-            const i32 l = keys[t];
-            if (l >= 0) bx = min(bx, cond_candidate(cnts[t], sa, a.bptr[l + 1] - a.bptr[l], n, inv_n));
+        for (int t = threadIdx.x; t < nf; t += BLK_WARPS * 32) {
+            const int h = used[t];
+            const i32 l = keys[h];
+            bx = min(bx, cond_candidate(cnts[h], sa, a.bptr[l + 1] - a.bptr[l], n, inv_n));
+            keys[h] = -1;
+            cnts[h] = 0;
         }
         for (int o = 16; o; o >>= 1) bx = min(bx, __shfl_xor_sync(FULL_MASK, bx, o));
         if (lane == 0) wmin[w] = bx;
@@ -389,33 +415,45 @@ __global__ void spill_sizes(const i64 *list, i64 nk, const i32 *active, const i6
     }
 }
 
-// Disjoint pairs that can be admitted (|A| + |B| > n/2): every active A
-// against the listed large communities B of its part; the pair is disjoint
-// unless a merge of the two sorted lists meets a common node.
+// Disjoint pairs that can be admitted (|A| + |B| > n/2).
+// The large communities of B grouped by part (boff: offsets per part), so
+// that an A community meets only those of its own part: warp per active A,
+// lanes over its part's list.
 __global__ void disjoint_pairs(const i64 *aptr, const i32 *anodes, const i32 *active, i64 n_active,
-                               const i64 *bptr, const i32 *bnodes, const i32 *big, i64 nbig, const i32 *acp,
-                               const i64 *acn, const i32 *bcp, unsigned long long *best) {
-    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < n_active * nbig; t += (i64)gridDim.x * blockDim.x) {
-        const i32 k = active[t / nbig];
-        const i32 l = big[t % nbig];
-        if (acp[k] != bcp[l]) continue;
-        const i64 sa = aptr[k + 1] - aptr[k], sb = bptr[l + 1] - bptr[l], n = acn[k];
-        if (2 * (sa + sb) <= n) continue;
-        const i32 *x = anodes + aptr[k], *y = bnodes + bptr[l];
-        i64 i = 0, j = 0;
-        bool meet = false;
-        while (i < sa && j < sb) {
-            if (x[i] < y[j]) ++i;
-            else if (x[i] > y[j]) ++j;
-            else {
-                meet = true;
-                break;
+                               const i64 *bptr, const i32 *bnodes, const i32 *big, const i64 *boff,
+                               const i32 *acp, const i64 *acn, unsigned long long *best) {
+    const int lane = threadIdx.x & 31;
+    const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
+    for (i64 q = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < n_active; q += warps) {
+        const i32 k = active[q];
+        const i32 p = acp[k];
+        const i64 sa = aptr[k + 1] - aptr[k], n = acn[k];
+        double bx = __builtin_huge_val();
+        for (i64 j = boff[p] + lane; j < boff[p + 1]; j += 32) {
+            const i32 l = big[j];
+            const i64 sb = bptr[l + 1] - bptr[l];
+            if (2 * (sa + sb) <= n) continue;
+            const i32 *x = anodes + aptr[k], *y = bnodes + bptr[l];
+            i64 i = 0, jj = 0;
+            bool meet = false;
+            while (i < sa && jj < sb) {
+                if (x[i] < y[jj]) ++i;
+                else if (x[i] > y[jj]) ++jj;
+                else {
+                    meet = true;
+                    break;
+                }
             }
+            if (!meet) bx = min(bx, cond_candidate(0, sa, sb, n, 1.0 / (double)n));
         }
-        if (meet) continue;
-        const double c = cond_candidate(0, sa, sb, n, 1.0 / (double)n);
-        if (c < __builtin_huge_val()) atomicMin(&best[k], min_bits(c));
+        for (int o = 16; o; o >>= 1) bx = min(bx, __shfl_xor_sync(FULL_MASK, bx, o));
+        if (lane == 0 && bx < __builtin_huge_val()) atomicMin(&best[k], min_bits(bx));
     }
+}
+
+__global__ void gather_parts(const i32 *big, i64 nbig, const i32 *cp, i32 *out) {
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < nbig; i += (i64)gridDim.x * blockDim.x)
+        out[i] = cp[big[i]];
 }
 
 // Communities with 2(|B| + 1) > n (n of B's part): the only ones that can
@@ -492,8 +530,10 @@ struct CommParts {
 };
 
 int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships &MB, const CommParts &PA,
-                  const CommParts &PB, const i32 *active, i64 n_active, unsigned long long *best, cudaStream_t st) {
-    i64 *spill = nullptr, *spill2 = nullptr, *tsz = nullptr, *toff = nullptr;
+                  const CommParts &PB, int32_t P, const i32 *active, i64 n_active, unsigned long long *best,
+                  cudaStream_t st) {
+    i64 *spill = nullptr, *spill2 = nullptr, *tsz = nullptr, *toff = nullptr, *dboff = nullptr;
+    i32 *bpart = nullptr;
     i32 *tkey = nullptr, *tcnt = nullptr, *big = nullptr;
     unsigned long long *cnt = nullptr;
     int rc = MSCD_OK;
@@ -526,7 +566,7 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
         if (nk > 0) {
             // middle tier: one community per CTA with a large shared-memory table
             if ((rc = dev_alloc(&spill2, nk, st))) break;
-            const size_t bsm = 2 * sizeof(i32) * BLK_TABLE;
+            const size_t bsm = 2 * sizeof(i32) * BLK_TABLE + sizeof(unsigned short) * (BLK_TABLE / 2);
             if ((rc = cuda_status(cudaFuncSetAttribute(pairs_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                        (int)bsm))))
                 break;
@@ -578,8 +618,30 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
             }
         }
         if (h[1] > 0) {
+            // group the large B communities by part (host counting sort: few)
+            const i64 nb = (i64)h[1];
+            std::vector<i32> hb(nb), hp(nb), sorted(nb);
+            std::vector<i64> boff(P + 1, 0);
+            if ((rc = dev_alloc(&bpart, nb, st))) break;
+            if ((rc = dev_alloc(&dboff, P + 1, st))) break;
+            gather_parts<<<GB, 256, 0, st>>>(big, nb, PB.cp, bpart); note_launch();
+            if ((rc = cuda_status(cudaMemcpyAsync(hb.data(), big, nb * sizeof(i32), cudaMemcpyDeviceToHost, st))))
+                break;
+            if ((rc = cuda_status(cudaMemcpyAsync(hp.data(), bpart, nb * sizeof(i32), cudaMemcpyDeviceToHost, st))))
+                break;
+            if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
+            for (i32 q : hp) boff[q + 1]++;
+            for (int32_t q = 0; q < P; ++q) boff[q + 1] += boff[q];
+            std::vector<i64> fillp(boff.begin(), boff.end() - 1);
+            for (i64 i = 0; i < nb; ++i) sorted[fillp[hp[i]]++] = hb[i];
+            if ((rc = cuda_status(cudaMemcpyAsync(big, sorted.data(), nb * sizeof(i32), cudaMemcpyHostToDevice, st))))
+                break;
+            if ((rc = cuda_status(cudaMemcpyAsync(dboff, boff.data(), (P + 1) * sizeof(i64), cudaMemcpyHostToDevice,
+                                                  st))))
+                break;
             disjoint_pairs<<<GB, 256, 0, st>>>(A.comm_ptr, A.comm_nodes, active, n_active, B.comm_ptr, B.comm_nodes,
-                                               big, (i64)h[1], PA.cp, PA.cn, PB.cp, best); note_launch();
+                                               big, dboff, PA.cp, PA.cn, best); note_launch();
+            if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;  // host vectors outlive the copies
         }
     } while (0);
     cudaFreeAsync(spill, st);
@@ -590,6 +652,8 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
     if (toff) cudaFreeAsync(toff, st);
     if (tkey) cudaFreeAsync(tkey, st);
     if (tcnt) cudaFreeAsync(tcnt, st);
+    if (bpart) cudaFreeAsync(bpart, st);
+    if (dboff) cudaFreeAsync(dboff, st);
     return rc;
 }
 
@@ -646,12 +710,12 @@ int nmi_between(const ScaleResult &X, const ScaleResult &Y, i64 n, const i64 *pa
         // H(X_k|Y) for the X communities without an identical partner
         if (na[0] > 0) {
             if ((rc = build_memberships(Y, n, &MY, st))) break;
-            if ((rc = one_direction(X, Y, MY, PX, PY, actX, (i64)na[0], bestX, st))) break;
+            if ((rc = one_direction(X, Y, MY, PX, PY, P, actX, (i64)na[0], bestX, st))) break;
         }
         // H(Y_l|X) likewise
         if (na[1] > 0) {
             if ((rc = build_memberships(X, n, &MX, st))) break;
-            if ((rc = one_direction(Y, X, MX, PY, PX, actY, (i64)na[1], bestY, st))) break;
+            if ((rc = one_direction(Y, X, MX, PY, PX, P, actY, (i64)na[1], bestY, st))) break;
         }
         normalise_sum<<<GB, 256, 0, st>>>(X.comm_ptr, CX, PX.cn, PX.cp, bestX, acc, acc + 4 * P); note_launch();
         normalise_sum<<<GB, 256, 0, st>>>(Y.comm_ptr, CY, PY.cn, PY.cp, bestY, acc + 2 * P, acc + 5 * P);
