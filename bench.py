@@ -674,6 +674,10 @@ def run_reference(args):
         return
     import oracle
 
+    if args.workload not in WORKLOADS and args.workload != "serve":
+        print(json.dumps({"impl": "reference", "unavailable": "the reference arm covers the lfr-100k, "
+                          "uneven-batch and serve workloads (the oracle on a bounded sample)"}), flush=True)
+        return
     wl = ServeSample(args) if args.workload == "serve" else WORKLOADS[args.workload](args)
     threads = os.cpu_count() or 1
     per_step = max(1.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))

@@ -40,6 +40,11 @@
 // on x86-64, long double on AArch64), then an exact tie test for the dyadic
 // rational alpha.  A case that none of these decides is reported as
 // ORC_EUNDECIDED.
+//
+// Besides the per-seed growth it states the paper's full method (Alg. 2 with
+// the growth of Alg. 3: seed rules, overlap pre-test, check and merge rounds,
+// carry-over across scales) in one fixed sequential order, orc_full below,
+// and growth from given initial members (orc_run_init).
 
 #include <algorithm>
 #include <atomic>

@@ -163,15 +163,18 @@ __global__ void __launch_bounds__(REACH_WARPS * 32) reach_smem(const i64 *cptr, 
                                                                i32 *partner, i32 *spill, unsigned long long *n_spill) {
     __shared__ i32 skey[REACH_WARPS][REACH_TABLE];
     __shared__ i32 scnt[REACH_WARPS][REACH_TABLE];
+    __shared__ unsigned short sused[REACH_WARPS][REACH_TABLE / 2];  // buckets claimed, in order
     __shared__ int sfill[REACH_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     i32 *keys = skey[w], *cnts = scnt[w];
+    unsigned short *used = sused[w];
+    for (int t = lane; t < REACH_TABLE; t += 32) {  // cleared once; afterwards only what was used
+        keys[t] = -1;
+        cnts[t] = 0;
+    }
+    __syncwarp();
     for (i64 q = (i64)blockIdx.x * REACH_WARPS + w; q < nl; q += (i64)gridDim.x * REACH_WARPS) {
         const i32 c = list[q];
-        for (int t = lane; t < REACH_TABLE; t += 32) {
-            keys[t] = -1;
-            cnts[t] = 0;
-        }
         if (lane == 0) sfill[w] = 0;
         __syncwarp();
         bool over = false;
@@ -186,7 +189,9 @@ __global__ void __launch_bounds__(REACH_WARPS * 32) reach_smem(const i64 *cptr, 
                     if (cur == -1) {
                         cur = atomicCAS(&keys[h], -1, o);
                         if (cur == -1) {
-                            if (atomicAdd(&sfill[w], 1) >= REACH_TABLE / 2) over = true;
+                            const int f = atomicAdd(&sfill[w], 1);
+                            if (f >= REACH_TABLE / 2) over = true;
+                            else used[f] = (unsigned short)h;
                             cur = o;
                         }
                     }
@@ -202,17 +207,25 @@ __global__ void __launch_bounds__(REACH_WARPS * 32) reach_smem(const i64 *cptr, 
         __syncwarp();
         if (over) {
             if (lane == 0) spill[atomicAdd(n_spill, 1ull)] = c;
+            for (int t = lane; t < REACH_TABLE; t += 32) {
+                keys[t] = -1;
+                cnts[t] = 0;
+            }
             __syncwarp();
             continue;
         }
+        const int nf = sfill[w];
         const i64 na = cptr[c + 1] - cptr[c];
         unsigned long long best = ~0ull;  // (position << 32) | partner
-        for (int t = lane; t < REACH_TABLE; t += 32) {
-            const i32 o = keys[t];
-            if (o < 0) continue;
+        for (int t = lane; t < nf; t += 32) {
+            const int h = used[t];
+            const i32 o = keys[h];
+            const i32 cnt = cnts[h];
+            keys[h] = -1;
+            cnts[h] = 0;
             const i64 nb = cptr[o + 1] - cptr[o];
             const i64 th = threshold(na, nb, eta);
-            if (cnts[t] < th) continue;
+            if (cnt < th) continue;
             const i64 pos = tth_common(cnodes + cptr[c], na, cnodes + cptr[o], nb, th);
             const unsigned long long key = ((unsigned long long)pos << 32) | (u32)o;
             best = min(best, key);
