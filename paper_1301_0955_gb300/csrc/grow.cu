@@ -141,9 +141,16 @@ struct Unit {
     bool err;    // probe bound hit (cannot happen at load <= 1/2)
 };
 
+template <class VT>
+struct SlotView {
+    VT din, kdeg;
+    unsigned char flag;
+};
+
 // Look up (and insert if absent) node v for every active lane.  Warp-collective.
 template <class VT, class HT, bool WEIGHTED>
-__device__ int lookup_insert(const State<VT, HT, WEIGHTED> &st, const DevGraph &G, Unit &U, i32 v, bool active) {
+__device__ int lookup_insert(const State<VT, HT, WEIGHTED> &st, const DevGraph &G, Unit &U, i32 v, bool active,
+                             SlotView<VT> *sv = nullptr) {
     const u32 hm = (u32)st.H - 1u;
     int slot = -1;
     u32 h = 0;
@@ -157,8 +164,21 @@ __device__ int lookup_insert(const State<VT, HT, WEIGHTED> &st, const DevGraph &
                 need = true;
                 break;
             }
-            if (st.id[x - 1] == v) {
+            const i32 idx = st.id[x - 1];
+            VT dv = 0, kd = 0;
+            unsigned char fl = 0;
+            if (sv) {  // loaded with the id: one dependent step after the bucket
+                dv = st.din[x - 1];
+                kd = st.kdeg[x - 1];
+                fl = st.flag[x - 1];
+            }
+            if (idx == v) {
                 slot = (int)x - 1;
+                if (sv) {
+                    sv->din = dv;
+                    sv->kdeg = kd;
+                    sv->flag = fl;
+                }
                 break;
             }
             h = (h + 1u) & hm;
@@ -175,11 +195,17 @@ __device__ int lookup_insert(const State<VT, HT, WEIGHTED> &st, const DevGraph &
         }
         if (need) {
             slot = U.ns + __popc(ball & lanemask_lt());
+            const VT kv = (VT)G.k[v];
             st.id[slot] = v;
             st.din[slot] = 0;
-            st.kdeg[slot] = (VT)G.k[v];
+            st.kdeg[slot] = kv;
             st.key[slot] = NEG_INF;
             st.flag[slot] = 0;
+            if (sv) {
+                sv->din = 0;
+                sv->kdeg = kv;
+                sv->flag = 0;
+            }
         }
         // Claim the empty buckets found.  Only this warp writes its table, so
         // lanes that found the same bucket are told apart with a match instead
@@ -453,22 +479,24 @@ __device__ void expand(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Uni
             v = G.col[e];
             w = WEIGHTED ? G.wfx[e] : 1;
         }
-        const int s = lookup_insert(st, G, U, v, act);
+        SlotView<VT> sv;
+        const int s = lookup_insert(st, G, U, v, act, &sv);
         if (U.ovf || U.err) return;
         bool upd = false;
         float k = NEG_INF;
+        i64 d = 0;
         if (act) {
-            const i64 d = (i64)st.din[s] + sign * w;
+            d = (i64)sv.din + sign * w;
             st.din[s] = (VT)d;
-            if (requeue && !(st.flag[s] & F_MEMBER)) {
-                k = rank_key(d, (i64)st.kdeg[s], U.alpha32);
+            if (requeue && !(sv.flag & F_MEMBER)) {
+                k = rank_key(d, (i64)sv.kdeg, U.alpha32);
                 st.key[s] = k;
                 upd = true;
             }
         }
         if (upd) {
             atomicMax(&st.gmax[s >> 5], ord(k));
-            atomicMax(&st.qmax[s >> 5], ord(__fdividef(exact::i2f((i64)st.din[s]), exact::i2f((i64)st.kdeg[s]))));
+            atomicMax(&st.qmax[s >> 5], ord(__fdividef(exact::i2f(d), exact::i2f((i64)sv.kdeg))));
         }
     }
     __syncwarp();

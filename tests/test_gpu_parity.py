@@ -322,3 +322,36 @@ def test_initial_members_parity(orc, ctx, small_class):
     c.free_graph(gid)
     if small_class:
         c.close()
+
+
+def test_hub_node_wide_slots(orc, ctx):
+    """A hub of degree 70,000 (degrees beyond 16 bits: 32-bit slot values) and
+    units touching more than 32,768 nodes (32-bit hash buckets), against the
+    oracle."""
+    rng = np.random.default_rng(17)
+    n = 70_001
+    leaves = np.arange(1, n, dtype=np.int64)
+    # the hub (node 0) joined to every leaf, leaves joined in small rings of 5
+    ring = leaves.reshape(-1, 5)
+    ea = [np.zeros(n - 1, np.int64), ring.ravel()]
+    eb = [leaves, np.roll(ring, -1, axis=1).ravel()]
+    extra = rng.integers(1, n, (2000, 2))
+    extra = extra[extra[:, 0] != extra[:, 1]]
+    ea.append(extra[:, 0])
+    eb.append(extra[:, 1])
+    a = np.concatenate(ea)
+    b = np.concatenate(eb)
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    key = np.unique(lo * n + hi)
+    rp, col, _ = synth.to_csr(n, key // n, key % n)
+    G = orc.Graph(n, rp, col)
+    assert G.status == 0
+    gid = ctx.load_csr(n, rp, col)
+    assert ctx.graph_info(gid)["n"] == n
+    seeds = np.array([0, 1, 2, 3, 5000, 69999], np.int32)
+    alphas = np.array([1.0, 0.5, 0.3])
+    assert ctx.run(gid, alphas, seeds) == 0
+    compare_units(orc, ctx, G, alphas, seeds, threads=4)
+    st = ctx.run_stats()
+    assert any(l["cap"] > 32768 for l in st["launches"])
+    ctx.free_graph(gid)
