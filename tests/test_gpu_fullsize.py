@@ -107,3 +107,43 @@ def test_lfr1m_weighted_sampled(orc, ctx):
     check_properties(ctx, seeds, len(alphas), g.n)
     check_sample(orc, ctx, G, alphas, seeds, 8, np.random.default_rng(7))
     ctx.free_graph(gid)
+
+
+def test_uneven_batch_quarter_sampled(orc, ctx):
+    """The uneven batch (256 two-level graphs, log-uniform sizes) at a quarter
+    of its node counts (2.3M nodes, 16 scales, 37M units), batched as one
+    disjoint union in the launch configuration of the benchmark: a seeded
+    sample of units of a seeded sample of parts against the oracle on the
+    part's own graph."""
+    import multiprocessing as mp
+
+    from paper_1301_0955_gb300 import mscd
+
+    specs = synth.uneven_batch_specs(256, seed=4, scale_nodes=0.25)
+    with mp.get_context("spawn").Pool(min(16, len(specs))) as pool:
+        graphs = pool.map(synth.graph_from_spec, specs, chunksize=1)
+    alphas = mscd.scales_logspaced(0.5, 1.0, 16)
+    gids = [ctx.load_csr(g.n, g.row_ptr, g.col) for g in graphs]
+    uid = ctx.graph_union(gids)
+    for gid in gids:
+        ctx.free_graph(gid)
+    off = ctx.graph_parts(uid)
+    assert ctx.run(uid, alphas) == mscd.OK
+    assert ctx.run_stats()["undecided"] == 0
+    rng = np.random.default_rng(99)
+    parts = np.sort(rng.choice(len(graphs), 12, replace=False))
+    for s in range(0, 16, 5):
+        for p in parts:
+            g = graphs[p]
+            o = int(off[p])
+            G = orc.Graph(g.n, g.row_ptr, g.col)
+            pick = np.sort(rng.choice(g.n, min(4, g.n), replace=False)).astype(np.int32)
+            rc, optr, onodes, of, ost = orc.run(G, [alphas[s]], pick, threads=8)
+            assert rc == 0
+            for t, j in enumerate(pick):
+                mem, f = ctx.membership(s, o + int(j))  # one unit at a time: the run holds 37M
+                assert np.array_equal(mem - o, onodes[optr[t]:optr[t + 1]]), (s, p, int(j))
+                assert f == pytest.approx(of[t], rel=F_RTOL, abs=0)
+    nmi, w3, w5 = ctx.stability(part=int(parts[0]))
+    assert np.all((nmi > -1e-12) & (nmi < 1 + 1e-12))
+    ctx.free_graph(uid)
