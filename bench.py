@@ -25,6 +25,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -119,7 +120,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # nvidia-smi samples of the timed region (BENCH_CLOCKS_CSV keeps them)
+        self.path = os.environ.get("BENCH_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), "bench_clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
