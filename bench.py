@@ -15,7 +15,7 @@ every node a seed: graph checks and exact weights, growth of all 2,000,000
              16 B per row visited) / growth time, against the measured HBM copy
              bandwidth
 
---impl reference times the CPU oracle (the reference arm of this build) on a
+--impl reference times the CPU oracle (the reference arm) on a
 bounded sample of the same workload.  Under torchrun every rank runs its own
 replica of the workload (weak scaling, no collective on the data path).
 """
