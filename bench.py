@@ -18,6 +18,12 @@ every node a seed: graph checks and exact weights, growth of all 2,000,000
 --impl reference times the CPU oracle (the reference arm) on a
 bounded sample of the same workload.  Under torchrun every rank runs its own
 replica of the workload (weak scaling, no collective on the data path).
+
+Other workloads (--workload): uneven-batch (256 graphs of log-uniform size as
+one disjoint union, 16 scales), serve (query server on four 2M-node graphs,
+Poisson arrivals at fractions of saturation, p50/p99 latency), full (the
+paper's whole Alg. 2 on the 100k-node graph) and accuracy (scale ranges where
+planted levels are found, in the shape of the paper's Table 1).
 """
 import argparse
 import hashlib
