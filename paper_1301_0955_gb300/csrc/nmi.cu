@@ -271,17 +271,20 @@ __global__ void __launch_bounds__(NMI_WARPS * 32) pairs_smem(DirArgs a) {
     }
 }
 
-// Warp per listed community (positions in `active`): the same with a global
-// table of its own.
-__global__ void pairs_global(DirArgs a, const i64 *list, i64 nk) {
-    const int lane = threadIdx.x & 31;
-    const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
-    for (i64 r = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nk; r += warps) {
+// CTA per listed community (positions in `active`): the same with a global
+// table of its own, the community's members spread over the CTA's warps (these
+// communities meet thousands of partners through millions of incidences).
+constexpr int GLB_WARPS = 16;
+
+__global__ void __launch_bounds__(GLB_WARPS * 32) pairs_global(DirArgs a, const i64 *list, i64 nk) {
+    __shared__ double wmin[GLB_WARPS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (i64 r = blockIdx.x; r < nk; r += gridDim.x) {
         const i32 k = a.active[list[r]];
         i32 *keys = a.tkey + a.toff[r];
         i32 *cnts = a.tcnt + a.toff[r];
         const u32 tm = (u32)(a.toff[r + 1] - a.toff[r] - 1);
-        for (i64 e = a.aptr[k]; e < a.aptr[k + 1]; ++e) {
+        for (i64 e = a.aptr[k] + w; e < a.aptr[k + 1]; e += GLB_WARPS) {
             const i32 u = a.anodes[e];
             for (i64 j = a.mptr[u] + lane; j < a.mptr[u + 1]; j += 32) {
                 const i32 l = a.mlist[j];
@@ -300,16 +303,23 @@ __global__ void pairs_global(DirArgs a, const i64 *list, i64 nk) {
                 }
             }
         }
-        __syncwarp();
+        __syncthreads();
         const i64 sa = a.aptr[k + 1] - a.aptr[k], n = a.acn[k];
         const double inv_n = 1.0 / (double)n;
-        double bx = __longlong_as_double((long long)a.best[k]);
-        for (u32 t = lane; t <= tm; t += 32) {
+        double bx = __builtin_huge_val();
+        for (u32 t = threadIdx.x; t <= tm; t += GLB_WARPS * 32) {
             const i32 l = keys[t];
             if (l >= 0) bx = min(bx, cond_candidate(cnts[t], sa, a.bptr[l + 1] - a.bptr[l], n, inv_n));
         }
         for (int o = 16; o; o >>= 1) bx = min(bx, __shfl_xor_sync(FULL_MASK, bx, o));
-        if (lane == 0) a.best[k] = min_bits(bx);
+        if (lane == 0) wmin[w] = bx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = __longlong_as_double((long long)a.best[k]);
+            for (int q = 0; q < GLB_WARPS; ++q) m = min(m, wmin[q]);
+            a.best[k] = min_bits(m);
+        }
+        __syncthreads();
     }
 }
 
@@ -611,7 +621,9 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
                     break;
                 if ((rc = cuda_status(cudaMemsetAsync(tkey, 0xff, TT * sizeof(i32), st)))) break;
                 if ((rc = cuda_status(cudaMemsetAsync(tcnt, 0, TT * sizeof(i32), st)))) break;
-                pairs_global<<<GB, 256, 0, st>>>(a, list + r0, r1 - r0); note_launch();
+                pairs_global<<<(unsigned)std::min<i64>(r1 - r0, 152 * 4), GLB_WARPS * 32, 0, st>>>(a, list + r0,
+                                                                                              r1 - r0);
+                note_launch();
                 // the host offsets are read by the copy before the next chunk rewrites them
                 if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
                 r0 = r1;
