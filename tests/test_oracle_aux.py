@@ -183,3 +183,27 @@ def test_window_means(orc):
     assert w5.tolist() == pytest.approx([0.15, 0.2, 0.25, 0.3, 0.35])
     one = orc.window_means(np.zeros(0), 1, 3)
     assert np.isnan(one[0])
+
+
+def test_nmi_hand_computed_two_covers(orc):
+    """A worked example of the overlapping NMI (Sec. 4): n = 4, X = {{0, 1}},
+    Y = {{0, 1, 2}}.  With h(p) = -p log2 p: H(X_1) = 1; H(Y_1) = h(3/4) +
+    h(1/4) = 2 - (3/4) log2 3.  The pair has P11 = 1/2, P10 = 0, P01 = 1/4,
+    P00 = 1/4, so h(P11) + h(P00) = 1 > h(P01) + h(P10) = 1/2 (admitted) and
+    H(X_1, Y_1) = 3/2.  Hence H(X_1|Y) = 3/2 - H(Y_1) (normalised by 1) and
+    H(Y_1|X) = 3/2 - 1 = 1/2 (normalised by H(Y_1)), and
+    N = 1 - [(3/2 - H(Y_1)) + 1 / (2 H(Y_1))] / 2."""
+    import math
+
+    HY = 2.0 - 0.75 * math.log2(3.0)
+    want = 1.0 - 0.5 * ((1.5 - HY) + 0.5 / HY)
+    a = (np.array([0, 2], np.int64), np.array([0, 1], np.int32))
+    b = (np.array([0, 3], np.int64), np.array([0, 1, 2], np.int32))
+    assert orc.nmi(4, *a, *b) == pytest.approx(want, abs=1e-15)
+    assert orc.nmi(4, *b, *a) == pytest.approx(want, abs=1e-15)
+    # adding to Y a community of the remaining node leaves X's term (its best
+    # partner is unchanged) and gives Y_2 = {3} a partner that is not admitted
+    # (disjoint, |X_1| + |Y_2| <= n/2), so H(Y_2|X) = H(Y_2), normalised 1
+    b2 = (np.array([0, 3, 4], np.int64), np.array([0, 1, 2, 3], np.int32))
+    want2 = 1.0 - 0.5 * ((1.5 - HY) + 0.5 * (0.5 / HY + 1.0))
+    assert orc.nmi(4, *a, *b2) == pytest.approx(want2, abs=1e-15)
