@@ -687,6 +687,9 @@ extern "C" int orc_dedup(i64 n_units, const i64 *ptr, const i32 *nodes, i64 *n_c
 // Readings: a community with H(X_k) = 0 (all n nodes) contributes 0; the
 // admission test is false when {n11, n00} and {n01, n10} are the same
 // multiset of counts (the two sides are then equal).
+// Parity partially unpinned: the paper cites this measure without printing
+// it; the tests pin identity, symmetry, relabelling, the zero cases and one
+// worked example in closed form, not a value the paper gives.
 // ---------------------------------------------------------------------------
 
 static double hlog(i64 c, i64 n) {
