@@ -264,6 +264,16 @@ int mscd_autotune(mscd_ctx *ctx, int32_t graph_id, const double *alphas, int32_t
  * Any pointer may be NULL. */
 int mscd_get_stability(mscd_ctx *ctx, double *nmi_succ, double *nmi_win3, double *nmi_win5);
 
+/* The window means of mscd_get_stability for any list of successive-scale
+ * NMI values (Sec. 4: "averaged over p successive scales"): out[i] is the
+ * mean of nmi_succ[j] (the pair of scales j, j+1) over the pairs inside the
+ * window of p scales centred on scale i, clipped at the ends; NaN when the
+ * window holds no pair.  nmi_succ host double[n_scales-1] (may be NULL when
+ * n_scales = 1), out host double[n_scales].  EINVAL unless n_scales >= 1 and
+ * p >= 2.  Host code only (no context, no GPU), e.g. for the NMI of merged
+ * shards (mscd_merge_shards + mscd_nmi_covers). */
+int mscd_window_means(const double *nmi_succ, int32_t n_scales, int32_t p, double *out);
+
 /* The same for part `part` of a union graph (mscd_graph_union); part 0 is what
  * mscd_get_stability returns.  A part without seeds in the run gets NaN.
  * EINVAL for a part outside the last run's graph. */
@@ -278,6 +288,42 @@ int mscd_get_run_stats(mscd_ctx *ctx, mscd_run_stats *out);
  * against a reference partition.  NaN if a cover is empty. */
 int mscd_nmi_covers(mscd_ctx *ctx, int64_t n, const int64_t *ptr_a, const int32_t *nodes_a, int64_t n_a,
                     const int64_t *ptr_b, const int32_t *nodes_b, int64_t n_b, double *nmi);
+
+/* ---- seeds split across GPUs --------------------------------------------
+ * Units are independent (each grows from its own seed, Alg. 1), so one job's
+ * seeds can be split across GPUs (one process each) and every process runs
+ * mscd_run on its share.  What each returns for a scale is its shard of the
+ * deduplicated communities; mscd_merge_shards joins the shards of one scale
+ * into exactly what one mscd_run over all the seeds returns for it: the
+ * distinct member lists, numbered in order of their smallest generating seed
+ * index in the whole job, and the community of every seed.  Host code only:
+ * it needs no context and no GPU, so it runs wherever the shards were
+ * gathered. */
+typedef struct mscd_cover_shard {
+    int64_t n_seeds;           /* seeds this shard grew                              */
+    const int64_t *seed_index; /* int64[n_seeds]: each seed's index in the whole job */
+    const int32_t *seed2comm;  /* int32[n_seeds]: its community in this shard        */
+    int64_t n_comms;           /* communities of this shard                          */
+    const int64_t *ptr;        /* int64[n_comms+1], ptr[0] = 0                       */
+    const int32_t *nodes;      /* int32[ptr[n_comms]], each list non-empty and
+                                  strictly ascending, ids >= 0                       */
+    const double *fitness;     /* double[n_comms], or NULL                           */
+} mscd_cover_shard;
+
+/* Merge n_shards shards of one scale (host pointers).  The seed indices of
+ * all shards together must be 0..n_seeds_total-1, each exactly once, and
+ * every community of a shard must be the community of one of its seeds;
+ * MSCD_EINVAL otherwise (also for a malformed list).  A list found in several
+ * shards is one community; its fitness is taken from the shard holding its
+ * smallest seed (the device computes f from exact integer sums, so every
+ * shard has the same value).  Outputs: ptr int64[n_comms+1] (ptr_cap
+ * entries), nodes int32[nodes_cap], fitness double[n_comms] (may be NULL;
+ * then shards may omit theirs), seed2comm int32[n_seeds_total] (may be
+ * NULL).  *n_comms and *n_nodes always get the sizes; a buffer too small
+ * gives MSCD_ESMALL and nothing else is written. */
+int mscd_merge_shards(const mscd_cover_shard *shards, int32_t n_shards, int64_t n_seeds_total, int64_t *ptr,
+                      int64_t ptr_cap, int32_t *nodes, int64_t nodes_cap, double *fitness, int32_t *seed2comm,
+                      int64_t *n_comms, int64_t *n_nodes);
 
 /* Where the last failed mscd_run stopped and why ("" if none failed), e.g.
  * "mscd_run: dedup of scale 3: device memory allocation failed".  The string

@@ -904,6 +904,15 @@ int mscd_get_stability(mscd_ctx *c, double *nmi_succ, double *nmi_win3, double *
     return mscd_get_stability_part(c, 0, nmi_succ, nmi_win3, nmi_win5);
 }
 
+int mscd_window_means(const double *nmi_succ, int32_t n_scales, int32_t p, double *out) {
+    if (n_scales < 1 || p < 2 || !out || (n_scales > 1 && !nmi_succ)) return MSCD_EINVAL;
+    std::vector<double> nmi, w;
+    if (n_scales > 1) nmi.assign(nmi_succ, nmi_succ + (n_scales - 1));
+    window_means(nmi, n_scales, p, w);
+    std::copy(w.begin(), w.end(), out);
+    return MSCD_OK;
+}
+
 const char *mscd_last_error(mscd_ctx *c) { return c ? c->last_error : ""; }
 
 int mscd_get_run_stats(mscd_ctx *c, mscd_run_stats *out) {

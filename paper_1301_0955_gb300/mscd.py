@@ -71,6 +71,11 @@ class mscd_run_stats(C.Structure):
         return d
 
 
+class mscd_cover_shard(C.Structure):
+    _fields_ = [("n_seeds", C.c_int64), ("seed_index", i64p), ("seed2comm", i32p), ("n_comms", C.c_int64),
+                ("ptr", i64p), ("nodes", i32p), ("fitness", f64p)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "mscd_strerror": (C.c_char_p, [C.c_int]),
@@ -108,6 +113,9 @@ SIGNATURES = {
     "mscd_get_run_stats": (C.c_int, [vp, C.POINTER(mscd_run_stats)]),
     "mscd_last_error": (C.c_char_p, [vp]),
     "mscd_nmi_covers": (C.c_int, [vp, C.c_int64, i64p, i32p, C.c_int64, i64p, i32p, C.c_int64, f64p]),
+    "mscd_window_means": (C.c_int, [f64p, C.c_int32, C.c_int32, f64p]),
+    "mscd_merge_shards": (C.c_int, [C.POINTER(mscd_cover_shard), C.c_int32, C.c_int64, i64p, C.c_int64, i32p,
+                                    C.c_int64, f64p, i32p, i64p, i64p]),
     "mscd_grow_noalloc": (C.c_int, [vp, C.c_int32, f64p, C.c_int32, vp, C.c_int64, vp, C.c_int64, vp, vp, vp, vp,
                                     vp, vp, i64p, vp]),
 }
@@ -162,6 +170,63 @@ def scales_logspaced(vmin: float, a: float, x: int) -> np.ndarray:
     out = np.zeros(max(x, 1), np.float64)
     _check(load().mscd_scales_logspaced(vmin, a, x, out.ctypes.data_as(f64p)), "mscd_scales_logspaced")
     return out
+
+
+def window_means(nmi_succ, n_scales: int, p: int) -> np.ndarray:
+    """mscd_window_means: means of successive-scale NMI over windows of p scales."""
+    a = np.ascontiguousarray(nmi_succ, np.float64)
+    out = np.zeros(max(n_scales, 1), np.float64)
+    _check(load().mscd_window_means(a.ctypes.data_as(f64p) if len(a) else None, n_scales, p,
+                                    out.ctypes.data_as(f64p)), "mscd_window_means")
+    return out
+
+
+def merge_shards(shards, n_seeds_total: int):
+    """mscd_merge_shards on host arrays.  shards: a list of dicts with
+    seed_index (int64), seed2comm (int32), ptr (int64), nodes (int32) and
+    optionally fitness (float64), e.g. ``Context.communities`` of each GPU's
+    share of the seeds.  Returns (ptr, nodes, fitness or None, seed2comm)."""
+    keep = []
+    arr = (mscd_cover_shard * max(len(shards), 1))()
+    with_f = all(s.get("fitness") is not None for s in shards)
+    for i, s in enumerate(shards):
+        si = np.ascontiguousarray(s["seed_index"], np.int64)
+        s2c = np.ascontiguousarray(s["seed2comm"], np.int32)
+        ptr = np.ascontiguousarray(s["ptr"], np.int64)
+        nodes = np.ascontiguousarray(s["nodes"], np.int32)
+        f = np.ascontiguousarray(s["fitness"], np.float64) if with_f else None
+        keep += [si, s2c, ptr, nodes, f]
+        arr[i] = mscd_cover_shard(len(si), si.ctypes.data_as(i64p), s2c.ctypes.data_as(i32p), len(ptr) - 1,
+                                  ptr.ctypes.data_as(i64p), nodes.ctypes.data_as(i32p),
+                                  f.ctypes.data_as(f64p) if f is not None else None)
+    nc, nn = C.c_int64(), C.c_int64()
+    rc = load().mscd_merge_shards(arr, len(shards), n_seeds_total, None, 0, None, 0, None, None, C.byref(nc),
+                                  C.byref(nn))
+    if rc not in (OK, ESMALL):
+        raise MscdError(rc, "mscd_merge_shards")
+    ptr = np.zeros(nc.value + 1, np.int64)
+    nodes = np.zeros(max(nn.value, 1), np.int32)
+    f = np.zeros(max(nc.value, 1), np.float64) if with_f else None
+    s2c = np.zeros(max(n_seeds_total, 1), np.int32)
+    _check(load().mscd_merge_shards(arr, len(shards), n_seeds_total, ptr.ctypes.data_as(i64p), nc.value + 1,
+                                    nodes.ctypes.data_as(i32p), nn.value,
+                                    f.ctypes.data_as(f64p) if with_f else None, s2c.ctypes.data_as(i32p),
+                                    C.byref(nc), C.byref(nn)), "mscd_merge_shards")
+    return ptr, nodes[: nn.value], (f[: nc.value] if with_f else None), s2c[:n_seeds_total]
+
+
+def shard_seeds(n_seeds: int, rank: int, world: int) -> np.ndarray:
+    """Indices into a job's seed list of one process's share when the seeds are
+    split across `world` GPUs: every world-th seed from `rank` (neighbouring
+    seeds, often of one community and of similar cost, go to different GPUs)."""
+    return np.arange(rank, n_seeds, world, dtype=np.int64)
+
+
+def merge_gathered(gathered, n_seeds_total: int):
+    """gathered[r][s]: rank r's shard of scale s (a dict for merge_shards).
+    Returns per scale the merged (ptr, nodes, fitness, seed2comm)."""
+    n_scales = len(gathered[0]) if gathered else 0
+    return [merge_shards([g[s] for g in gathered], n_seeds_total) for s in range(n_scales)]
 
 
 class Context:
@@ -442,6 +507,36 @@ class Context:
                                            s2c.ctypes.data_as(i32p), C.byref(nc), C.byref(nn)),
                "mscd_get_communities")
         return ptr, nodes[: nn.value], f[: nc.value], s2c[: self.n_seeds]
+
+    def run_sharded(self, gid: int, alphas, seeds, rank: int, world: int, all_gather):
+        """One job whose seeds are split across `world` processes, one GPU each.
+        This process grows its share (shard_seeds) with mscd_run; the shards of
+        every scale are exchanged with all_gather(obj) -> [obj of rank 0, ...]
+        (e.g. around torch.distributed.all_gather_object) and merged with
+        mscd_merge_shards, giving what one run over all the seeds gives; the
+        stability between successive merged scales is computed by
+        mscd_nmi_covers and mscd_window_means (on a graph that is not a union,
+        the values of mscd_get_stability).  Returns dict(status, communities =
+        [(ptr, nodes, fitness, seed2comm)] per scale, nmi, win3, win5)."""
+        alphas = np.ascontiguousarray(alphas, np.float64)
+        seeds = np.ascontiguousarray(seeds, np.int32)
+        idx = shard_seeds(len(seeds), rank, world)
+        rc, local = OK, []
+        if len(idx) == 0:  # more processes than seeds: an empty share
+            none = dict(seed_index=idx, seed2comm=np.zeros(0, np.int32), ptr=np.zeros(1, np.int64),
+                        nodes=np.zeros(0, np.int32), fitness=np.zeros(0, np.float64))
+            local = [none] * len(alphas)
+        else:
+            rc = self.run(gid, alphas, np.ascontiguousarray(seeds[idx]))
+            for s in range(len(alphas)):
+                ptr, nodes, f, s2c = self.communities(s)
+                local.append(dict(seed_index=idx, seed2comm=s2c, ptr=ptr, nodes=nodes, fitness=f))
+        merged = merge_gathered(all_gather(local), len(seeds))
+        n = self.graph_info(gid)["n"]
+        nmi = np.array([self.nmi_covers(n, merged[s][:2], merged[s + 1][:2]) for s in range(len(alphas) - 1)],
+                       np.float64)
+        return dict(status=rc, communities=merged, nmi=nmi, win3=window_means(nmi, len(alphas), 3),
+                    win5=window_means(nmi, len(alphas), 5))
 
     def stability(self, part=None):
         """(nmi_succ, window-3 means, window-5 means) of the last run, or of one
