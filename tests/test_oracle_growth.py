@@ -7,6 +7,8 @@ What fixes the expected values here, independently of the oracle:
   (big integers for dyadic alpha, 300-bit mpmath otherwise): the result is a
   local optimum for single additions and single non-seed removals, and equals
   the global optimum where the seed's component is a clique;
+* closed forms on barbells (two cliques joined by one edge): the growth
+  stops at the bridge where the closed-form add test of the partner fails;
 * invariants: the seed is always a member; results do not depend on the
   number of threads;
 * planted recovery on the 1,000-node planted partition: the micro and macro
@@ -185,6 +187,67 @@ def test_disjoint_cliques_reach_global_optimum(orc, alpha):
             mem, f, st, rc = orc.grow(g, seed, alpha)
             assert mem.tolist() == list(range(base, base + m))
         base += m
+
+
+def _f(K, V, alpha):
+    import mpmath as mp
+
+    return mp.mpf(0) if K == 0 else mp.mpf(K) / mp.power(mp.mpf(V), mp.mpf(alpha))
+
+
+def _barbell_conditions(m, alpha):
+    """Closed forms for two K_m joined by the bridge (m-1, m), grown from a seed
+    in the first clique A = {0..m-1}: (i) every addition of an A node improves
+    f, whatever A nodes are already in (K = j(j-1), V = sum of their degrees,
+    m-1 for a plain A node and m for the bridge end); (ii) at c = A the bridge
+    partner m (d = 1, k = m) fails the add test; (iii) no A node passes the
+    remove test at c = A.  A nodes always rank before node m (d >= 1 with
+    k <= m against d = 1 with k = m), so (i)-(iii) make the result exactly A."""
+    import mpmath as mp
+
+    mp.mp.prec = 300
+    adds_ok = True
+    for plain in range(0, m):          # plain A nodes in c
+        for bridge in (0, 1):          # the bridge end m-1 in c
+            j = plain + bridge
+            if j == 0 or j == m:
+                continue
+            K, V = j * (j - 1), plain * (m - 1) + bridge * m
+            cands = ([m - 1] if plain < m - 1 else []) + ([m] if not bridge else [])
+            adds_ok &= all(_f(K + 2 * j, V + k, alpha) > _f(K, V, alpha) for k in cands)
+    K, V = m * (m - 1), m * (m - 1) + 1
+    bridge_fails = not _f(K + 2, V + m, alpha) > _f(K, V, alpha)
+    no_removal = all(not _f(K - 2 * (m - 1), V - k, alpha) > _f(K, V, alpha) for k in (m - 1, m))
+    return adds_ok, bridge_fails, no_removal
+
+
+@pytest.mark.parametrize("m", [3, 4, 5, 7])
+@pytest.mark.parametrize("alpha", [0.5, 0.6, 0.75, 0.9, 1.0])
+def test_barbell_closed_form(orc, m, alpha):
+    """Two m-cliques joined by one edge.  Where the closed-form conditions hold
+    the growth from any seed of a clique returns exactly that clique with
+    f = m(m-1) / (m(m-1)+1)^alpha (not the global optimum at alpha = 1, which
+    is the whole graph with f = 1: the greedy stops at the bridge); where only
+    the bridge test flips, the partner across the bridge joins."""
+    edges = [(i, j) for i, j in itertools.combinations(range(m), 2)]
+    edges += [(m + i, m + j) for i, j in itertools.combinations(range(m), 2)]
+    edges += [(m - 1, m)]
+    g, _, _ = graph_from_edges(orc, 2 * m, edges)
+    adds_ok, bridge_fails, no_removal = _barbell_conditions(m, alpha)
+    K, V = m * (m - 1), m * (m - 1) + 1
+    for seed in range(2 * m):
+        mem, f, st, rc = orc.grow(g, seed, alpha)
+        assert rc == 0 and seed in mem.tolist()
+        own = list(range(m)) if seed < m else list(range(m, 2 * m))
+        partner = m if seed < m else m - 1
+        if adds_ok and bridge_fails and no_removal:
+            assert mem.tolist() == own
+            assert st["K"] == K and st["V"] == V
+            assert f == pytest.approx(float(_f(K, V, alpha)), rel=1e-15)
+        elif adds_ok and not bridge_fails:
+            assert partner in mem.tolist() and set(own) <= set(mem.tolist())
+    if (m, alpha) in ((5, 1.0), (7, 0.5)):
+        assert adds_ok and bridge_fails and no_removal  # the exact case is exercised
 
 
 def test_thread_count_independent(orc):
