@@ -324,6 +324,43 @@ def test_initial_members_parity(orc, ctx, small_class):
         c.close()
 
 
+def structured_graphs():
+    """Symmetric graphs where ranking and fitness ties are the rule (the
+    smaller-id rule and the strict tests decide most steps; the torus,
+    hypercube and complete bipartite graph send thousands of decisions to the
+    exact tie test), and a ring and a wheel whose units grow to every node."""
+    out = {}
+    n = 1000
+    out["ring1000"] = (n, [(i, (i + 1) % n) for i in range(n)])
+    r_, c_ = 30, 30
+    out["torus30x30"] = (r_ * c_, [(r * c_ + c, r * c_ + (c + 1) % c_) for r in range(r_) for c in range(c_)]
+                         + [(r * c_ + c, ((r + 1) % r_) * c_ + c) for r in range(r_) for c in range(c_)])
+    out["hypercube10"] = (1024, [(i, i ^ (1 << b)) for i in range(1024) for b in range(10) if i < i ^ (1 << b)])
+    out["K20,30"] = (50, [(i, 20 + j) for i in range(20) for j in range(30)])
+    out["K60"] = (60, list(itertools.combinations(range(60), 2)))
+    cav = [(10 * c + i, 10 * c + j) for c in range(50) for i, j in itertools.combinations(range(10), 2)]
+    out["caveman50x10"] = (500, cav + [(10 * c + 9, (10 * c + 10) % 500) for c in range(50)])
+    out["wheel500"] = (501, [(0, i) for i in range(1, 501)] + [(i, i % 500 + 1) for i in range(1, 501)])
+    return out
+
+
+@pytest.mark.parametrize("name", sorted(structured_graphs()))
+def test_structured_tie_graphs(orc, ctx, name):
+    n, edges = structured_graphs()[name]
+    e = np.asarray(edges, np.int64)
+    lo, hi = np.minimum(e[:, 0], e[:, 1]), np.maximum(e[:, 0], e[:, 1])
+    key = np.unique(lo * n + hi)
+    rp, col, _ = synth.to_csr(n, key // n, key % n)
+    G = orc.Graph(n, rp, col)
+    assert G.status == 0
+    gid = ctx.load_csr(n, rp, col)
+    alphas = np.array([1.0, 0.5, 0.75, 0.3, 1.5])
+    seeds = np.arange(n, dtype=np.int32)
+    assert ctx.run(gid, alphas, seeds) == 0
+    compare_units(orc, ctx, G, alphas, seeds, threads=8)
+    ctx.free_graph(gid)
+
+
 def test_hub_node_wide_slots(orc, ctx):
     """A hub of degree 70,000 (degrees beyond 16 bits: 32-bit slot values) and
     units touching more than 32,768 nodes (32-bit hash buckets), against the

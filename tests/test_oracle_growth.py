@@ -171,6 +171,80 @@ def test_bruteforce_local_optimum(orc, alpha):
     assert checked > 200
 
 
+def structured_graphs():
+    """Small graphs whose symmetry makes ranking and fitness ties common: the
+    smaller-id rule and the strict tests decide most steps."""
+    out = {}
+    for n in (5, 8, 12):
+        out["ring%d" % n] = (n, [(i, (i + 1) % n) for i in range(n)])
+        out["path%d" % n] = (n, [(i, i + 1) for i in range(n - 1)])
+    out["grid3x4"] = (12, [(r * 4 + c, r * 4 + c + 1) for r in range(3) for c in range(3)]
+                      + [(r * 4 + c, (r + 1) * 4 + c) for r in range(2) for c in range(4)])
+    out["torus3x4"] = (12, [(r * 4 + c, r * 4 + (c + 1) % 4) for r in range(3) for c in range(4)]
+                       + [(r * 4 + c, ((r + 1) % 3) * 4 + c) for r in range(3) for c in range(4)])
+    out["K3,4"] = (7, [(i, 3 + j) for i in range(3) for j in range(4)])
+    out["K2,5"] = (7, [(i, 2 + j) for i in range(2) for j in range(5)])
+    out["cube"] = (8, [(i, i ^ (1 << b)) for i in range(8) for b in range(3) if i < i ^ (1 << b)])
+    out["petersen"] = (10, [(i, (i + 1) % 5) for i in range(5)] + [(5 + i, 5 + (i + 2) % 5) for i in range(5)]
+                       + [(i, 5 + i) for i in range(5)])
+    out["wheel9"] = (10, [(0, i) for i in range(1, 10)] + [(i, i % 9 + 1) for i in range(1, 10)])
+    out["octahedron"] = (6, [(i, j) for i, j in itertools.combinations(range(6), 2) if j != i + 3])
+    out["bowtie"] = (5, [(0, 1), (1, 2), (0, 2), (2, 3), (3, 4), (2, 4)])
+    out["caveman4x3"] = (12, [(3 * c + i, 3 * c + j) for c in range(4) for i, j in itertools.combinations(range(3), 2)]
+                         + [(3 * c + 2, (3 * c + 3) % 12) for c in range(4)])
+    return out
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.5, 0.75, 0.625, 0.6180339887498949])
+@pytest.mark.parametrize("name", sorted(structured_graphs()))
+def test_structured_graphs_local_optimum(orc, name, alpha):
+    """Symmetric small graphs (rings, paths, grids, tori, complete bipartite,
+    cube, Petersen, wheel, octahedron, bowtie, caveman): from every seed the
+    result is a local optimum for single moves, checked with exact f, and is
+    never above the global optimum over subsets containing the seed."""
+    n, edges = structured_graphs()[name]
+    edges = sorted({(min(a, b), max(a, b)) for a, b in edges})
+    g, _, _ = graph_from_edges(orc, n, edges)
+    adj = [dict() for _ in range(n)]
+    for a, b in edges:
+        adj[a][b] = adj[b][a] = 1
+    k = [len(adj[u]) for u in range(n)]
+    for seed in range(n):
+        mem, f, st, rc = orc.grow(g, seed, alpha)
+        assert rc == 0
+        c = set(mem.tolist())
+        assert seed in c
+        K, V = kv(adj, k, c)
+        assert (K, V) == (st["K"], st["V"])
+        for u in range(n):
+            if u == seed:
+                continue
+            K2, V2 = kv(adj, k, c - {u} if u in c else c | {u})
+            assert not f_greater(K2, V2, K, V, alpha), (name, seed, alpha, sorted(c), u)
+        others = [u for u in range(n) if u != seed]
+        best = (0, 1)
+        for r in range(len(others) + 1):
+            for sub in itertools.combinations(others, r):
+                K2, V2 = kv(adj, k, set(sub) | {seed})
+                if f_greater(K2, V2, *best, alpha):
+                    best = (K2, V2)
+        assert not f_greater(K, V, *best, alpha)
+
+
+def test_ring_closed_form(orc):
+    """On a ring every node has degree 2; from {s} the two neighbours tie in
+    rank (d = 1, k = 2) and the smaller id is popped first.  At alpha = 1 a
+    path of j nodes has f = 2(j-1)/(2j), which rises with j, so the whole ring
+    is grown (f = 1); at alpha = 0.5 the same holds (2(j-1)/sqrt(2j) rises)."""
+    n = 9
+    g, _, _ = graph_from_edges(orc, n, [(i, (i + 1) % n) for i in range(n)])
+    for alpha in (1.0, 0.5):
+        for seed in range(n):
+            mem, f, st, rc = orc.grow(g, seed, alpha)
+            assert mem.tolist() == list(range(n))
+            assert f == pytest.approx((2 * n) ** (1 - alpha), rel=1e-15)
+
+
 @pytest.mark.parametrize("alpha", [0.5, 0.75, 1.0])
 def test_disjoint_cliques_reach_global_optimum(orc, alpha):
     """The seed's component is a clique: growth returns exactly that clique, the
