@@ -76,3 +76,23 @@ def test_full_method_initial_communities_and_eta(orc, ctx):
     init = (np.concatenate([[0], np.cumsum([len(x) for x in lists])]).astype(np.int64),
             np.concatenate(lists).astype(np.int32))
     compare(orc, ctx, g, [1.0, 0.7], init=init, eta=0.3)
+
+
+@pytest.mark.parametrize("name", ["hypercube10", "torus30x30", "ring1000", "K20,30"])
+@pytest.mark.parametrize("rule", [1, 2])
+def test_full_method_symmetric_graphs(orc, ctx, name, rule):
+    """Tie-heavy graphs: many overlapping equal-fitness communities meet the
+    merge check (the 10-cube merges over seven iterations at the finest
+    scale, the torus and the ring collapse into one community)."""
+    from types import SimpleNamespace
+
+    from test_gpu_parity import structured_graphs
+
+    n, edges = structured_graphs()[name]
+    e = np.asarray(edges, np.int64)
+    lo, hi = np.minimum(e[:, 0], e[:, 1]), np.maximum(e[:, 0], e[:, 1])
+    key = np.unique(lo * n + hi)
+    rp, col, _ = synth.to_csr(n, key // n, key % n)
+    g = SimpleNamespace(n=n, row_ptr=rp, col=col, w=None)
+    prio = np.random.default_rng(2).permutation(n).astype(np.int32)
+    compare(orc, ctx, g, [1.0, 0.75, 0.5], rule, prio)
