@@ -21,6 +21,10 @@
 //     s = (|A| + |B|)/n <= 1/2: h(P00) = h(1-s) <= h(s) (h(1-s) <= h(s)
 //     on [0, 1/2]) <= h(P10) + h(P01) (h concave with h(0) = 0 is
 //     subadditive), and h(P11) = 0, so the admission test fails.
+//     Either side of such a pair may be the small one, so the partners
+//     listed for this test are the B communities with 2(|B| + a) > n, a the
+//     largest active A community of the part; each A community walks its
+//     part's list in descending size and stops at the first B too small.
 // The intersections of the sharing pairs are counted by a warp per community:
 // it walks its members' lists of partner communities (the lanes spread over
 // one list at a time, whose entries are distinct) and counts in a
@@ -426,9 +430,10 @@ __global__ void spill_sizes(const i64 *list, i64 nk, const i32 *active, const i6
 }
 
 // Disjoint pairs that can be admitted (|A| + |B| > n/2).
-// The large communities of B grouped by part (boff: offsets per part), so
-// that an A community meets only those of its own part: warp per active A,
-// lanes over its part's list.
+// The candidate B communities grouped by part (boff: offsets per part) and
+// in descending size inside a part, so that an A community meets only those
+// of its own part and stops at the first one with 2(|A| + |B|) <= n: warp
+// per active A, lanes over its part's list.
 __global__ void disjoint_pairs(const i64 *aptr, const i32 *anodes, const i32 *active, i64 n_active,
                                const i64 *bptr, const i32 *bnodes, const i32 *big, const i64 *boff,
                                const i32 *acp, const i64 *acn, unsigned long long *best) {
@@ -442,7 +447,7 @@ __global__ void disjoint_pairs(const i64 *aptr, const i32 *anodes, const i32 *ac
         for (i64 j = boff[p] + lane; j < boff[p + 1]; j += 32) {
             const i32 l = big[j];
             const i64 sb = bptr[l + 1] - bptr[l];
-            if (2 * (sa + sb) <= n) continue;
+            if (2 * (sa + sb) <= n) break;  // every later entry of this lane is smaller
             const i32 *x = anodes + aptr[k], *y = bnodes + bptr[l];
             i64 i = 0, jj = 0;
             bool meet = false;
@@ -461,16 +466,31 @@ __global__ void disjoint_pairs(const i64 *aptr, const i32 *anodes, const i32 *ac
     }
 }
 
-__global__ void gather_parts(const i32 *big, i64 nbig, const i32 *cp, i32 *out) {
-    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < nbig; i += (i64)gridDim.x * blockDim.x)
+__global__ void gather_parts(const i32 *big, i64 nbig, const i32 *cp, const i64 *ptr, i32 *out, i64 *size) {
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < nbig; i += (i64)gridDim.x * blockDim.x) {
         out[i] = cp[big[i]];
+        size[i] = ptr[big[i] + 1] - ptr[big[i]];
+    }
 }
 
-// Communities with 2(|B| + 1) > n (n of B's part): the only ones that can
-// satisfy the disjoint admission condition with a community of size >= 1.
-__global__ void list_big(const i64 *ptr, i64 C, const i64 *cn, i32 *big, unsigned long long *nbig) {
-    for (i64 l = (i64)blockIdx.x * blockDim.x + threadIdx.x; l < C; l += (i64)gridDim.x * blockDim.x)
-        if (2 * (ptr[l + 1] - ptr[l] + 1) > cn[l]) big[atomicAdd(nbig, 1ull)] = (i32)l;
+// Largest active A community of every part.
+__global__ void active_max_size(const i64 *aptr, const i32 *active, i64 n_active, const i32 *acp,
+                                unsigned long long *amax) {
+    for (i64 q = (i64)blockIdx.x * blockDim.x + threadIdx.x; q < n_active; q += (i64)gridDim.x * blockDim.x) {
+        const i32 k = active[q];
+        atomicMax(&amax[acp[k]], (unsigned long long)(aptr[k + 1] - aptr[k]));
+    }
+}
+
+// B communities with 2(|B| + a) > n (n of B's part, a the largest active A
+// community of that part): the only ones that can meet an active A community
+// of their part in an admitted disjoint pair.
+__global__ void list_big(const i64 *ptr, i64 C, const i32 *cp, const i64 *cn, const unsigned long long *amax,
+                         i32 *big, unsigned long long *nbig) {
+    for (i64 l = (i64)blockIdx.x * blockDim.x + threadIdx.x; l < C; l += (i64)gridDim.x * blockDim.x) {
+        const i64 a = (i64)amax[cp[l]];
+        if (a > 0 && 2 * (ptr[l + 1] - ptr[l] + a) > cn[l]) big[atomicAdd(nbig, 1ull)] = (i32)l;
+    }
 }
 
 // Normalised term H(A_k|B) / H(A_k) in [0, 1] (the minimum never exceeds its
@@ -542,17 +562,19 @@ struct CommParts {
 int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships &MB, const CommParts &PA,
                   const CommParts &PB, int32_t P, const i32 *active, i64 n_active, unsigned long long *best,
                   cudaStream_t st) {
-    i64 *spill = nullptr, *spill2 = nullptr, *tsz = nullptr, *toff = nullptr, *dboff = nullptr;
+    i64 *spill = nullptr, *spill2 = nullptr, *tsz = nullptr, *toff = nullptr, *dboff = nullptr, *bsize = nullptr;
     i32 *bpart = nullptr;
     i32 *tkey = nullptr, *tcnt = nullptr, *big = nullptr;
-    unsigned long long *cnt = nullptr;
+    unsigned long long *cnt = nullptr, *amax = nullptr;
     int rc = MSCD_OK;
     do {
         if (n_active == 0) break;
         if ((rc = dev_alloc(&spill, n_active, st))) break;
         if ((rc = dev_alloc(&cnt, 3, st))) break;
         if ((rc = dev_alloc(&big, B.n_comms, st))) break;
+        if ((rc = dev_alloc(&amax, P, st))) break;
         if ((rc = cuda_status(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), st)))) break;
+        if ((rc = cuda_status(cudaMemsetAsync(amax, 0, (size_t)P * sizeof(unsigned long long), st)))) break;
         DirArgs a{};
         a.aptr = A.comm_ptr;
         a.anodes = A.comm_nodes;
@@ -567,7 +589,8 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
         a.n_spill = cnt;
         pairs_smem<<<(unsigned)std::min<i64>((n_active + NMI_WARPS - 1) / NMI_WARPS, 152 * 3), NMI_WARPS * 32, 0,
                      st>>>(a); note_launch();
-        list_big<<<GB, 256, 0, st>>>(B.comm_ptr, B.n_comms, PB.cn, big, cnt + 1); note_launch();
+        active_max_size<<<GB, 256, 0, st>>>(A.comm_ptr, active, n_active, PA.cp, amax); note_launch();
+        list_big<<<GB, 256, 0, st>>>(B.comm_ptr, B.n_comms, PB.cp, PB.cn, amax, big, cnt + 1); note_launch();
         unsigned long long h[2] = {0, 0};
         if ((rc = cuda_status(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st)))) break;
         if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
@@ -630,22 +653,34 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
             }
         }
         if (h[1] > 0) {
-            // group the large B communities by part (host counting sort: few)
+            // group the candidate B communities by part, in descending size
+            // inside a part (host sort: they are few)
             const i64 nb = (i64)h[1];
             std::vector<i32> hb(nb), hp(nb), sorted(nb);
+            std::vector<i64> hsz(nb), order(nb);
             std::vector<i64> boff(P + 1, 0);
             if ((rc = dev_alloc(&bpart, nb, st))) break;
+            if ((rc = dev_alloc(&bsize, nb, st))) break;
             if ((rc = dev_alloc(&dboff, P + 1, st))) break;
-            gather_parts<<<GB, 256, 0, st>>>(big, nb, PB.cp, bpart); note_launch();
+            gather_parts<<<GB, 256, 0, st>>>(big, nb, PB.cp, B.comm_ptr, bpart, bsize); note_launch();
             if ((rc = cuda_status(cudaMemcpyAsync(hb.data(), big, nb * sizeof(i32), cudaMemcpyDeviceToHost, st))))
                 break;
             if ((rc = cuda_status(cudaMemcpyAsync(hp.data(), bpart, nb * sizeof(i32), cudaMemcpyDeviceToHost, st))))
                 break;
+            if ((rc = cuda_status(cudaMemcpyAsync(hsz.data(), bsize, nb * sizeof(i64), cudaMemcpyDeviceToHost, st))))
+                break;
             if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
-            for (i32 q : hp) boff[q + 1]++;
+            for (i64 i = 0; i < nb; ++i) order[i] = i;
+            std::sort(order.begin(), order.end(), [&](i64 x, i64 y) {
+                if (hp[x] != hp[y]) return hp[x] < hp[y];
+                if (hsz[x] != hsz[y]) return hsz[x] > hsz[y];
+                return hb[x] < hb[y];
+            });
+            for (i64 i = 0; i < nb; ++i) {
+                sorted[i] = hb[order[i]];
+                boff[hp[i] + 1]++;
+            }
             for (int32_t q = 0; q < P; ++q) boff[q + 1] += boff[q];
-            std::vector<i64> fillp(boff.begin(), boff.end() - 1);
-            for (i64 i = 0; i < nb; ++i) sorted[fillp[hp[i]]++] = hb[i];
             if ((rc = cuda_status(cudaMemcpyAsync(big, sorted.data(), nb * sizeof(i32), cudaMemcpyHostToDevice, st))))
                 break;
             if ((rc = cuda_status(cudaMemcpyAsync(dboff, boff.data(), (P + 1) * sizeof(i64), cudaMemcpyHostToDevice,
@@ -665,7 +700,9 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
     if (tkey) cudaFreeAsync(tkey, st);
     if (tcnt) cudaFreeAsync(tcnt, st);
     if (bpart) cudaFreeAsync(bpart, st);
+    if (bsize) cudaFreeAsync(bsize, st);
     if (dboff) cudaFreeAsync(dboff, st);
+    if (amax) cudaFreeAsync(amax, st);
     return rc;
 }
 
