@@ -106,6 +106,12 @@ def whole_job_rate(units_per_rank, steps, world, max_total_ms):
     return world * units_per_rank * steps / (max_total_ms / 1e3)
 
 
+def require_ok(rc, what):
+    """A timed step whose call did not return MSCD_OK (0) is not a measurement."""
+    if rc != 0:
+        raise RuntimeError("%s returned status %d" % (what, rc))
+
+
 def source_hash():
     h = hashlib.sha256()
     for f in GROW_SOURCES:
@@ -280,13 +286,13 @@ class Lfr100k:
     def step_resident(self, ctx, stream):
         gid = ctx.load_csr(self.g.n, self.rp_d, self.col_d)
         rc = ctx.run(gid, self.alphas_d, self.seeds_d, stream=stream)
-        assert rc == self.mscd.OK, rc
+        require_ok(rc, "mscd_run")
         ctx.free_graph(gid)
 
     def step_e2e(self, ctx):
         gid = ctx.load_csr(self.g.n, self.rp_h, self.col_h)
         rc = ctx.run(gid, self.alphas, self.seeds_h)
-        assert rc == self.mscd.OK, rc
+        require_ok(rc, "mscd_run")
         nb = read_results(ctx, self.n_scales, 1)
         ctx.free_graph(gid)
         return nb
@@ -343,7 +349,7 @@ class UnevenBatch:
         for gid in gids:
             ctx.free_graph(gid)
         rc = ctx.run(uid, alphas, None, stream=stream)
-        assert rc == self.mscd.OK, rc
+        require_ok(rc, "mscd_run")
         return uid
 
     def step_resident(self, ctx, stream):
@@ -360,7 +366,7 @@ class UnevenBatch:
         for g, (rp, col) in zip(self.graphs, self.dev_parts):
             gid = ctx.load_csr(g.n, rp, col)
             rc = ctx.run(gid, self.alphas_d, None, stream=stream)
-            assert rc == self.mscd.OK, rc
+            require_ok(rc, "mscd_run")
             ctx.free_graph(gid)
 
     def cpu_baseline(self, seconds, threads):
@@ -395,7 +401,7 @@ def serve_phase(ctx, gids, alphas, queries, rate_qps):
         done = [q for q in list(out) if ctx.poll(q) == 2]
         for q in done:
             ptr, nodes, f, t, rc = ctx.result(q, out.pop(q))
-            assert rc == 0, rc
+            require_ok(rc, "mscd_query_result")
             lat.append(t[2])
             queued.append(t[0])
         if not done:
@@ -426,7 +432,7 @@ def run_full(args):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        assert ctx.full_run(gid, alphas, prio=prio, seed_rule=args.full_rule) == mscd.OK
+        require_ok(ctx.full_run(gid, alphas, prio=prio, seed_rule=args.full_rule), "mscd_full_run")
 
     for _ in range(args.warmup):
         step()

@@ -159,10 +159,12 @@ def _ptr(a):
     if a is None:
         return None, False
     if isinstance(a, np.ndarray):
-        assert a.flags["C_CONTIGUOUS"]
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to libmscd must be C-contiguous")
         return a.ctypes.data, False
     # torch tensor
-    assert a.is_contiguous()
+    if not a.is_contiguous():
+        raise ValueError("tensors passed to libmscd must be contiguous")
     return a.data_ptr(), bool(a.is_cuda)
 
 
@@ -260,7 +262,8 @@ class Context:
         rp, dev = _ptr(row_ptr)
         cp, dev2 = _ptr(col)
         wp, dev3 = _ptr(w)
-        assert dev == dev2 and (w is None or dev3 == dev)
+        if dev != dev2 or (w is not None and dev3 != dev):
+            raise ValueError("row_ptr, col and w must all be host or all be device arrays")
         gid = C.c_int32(-1)
         rc = load().mscd_graph_load_csr(self.h, int(n), rp, cp, wp, DEVICE_PTRS if dev else 0, C.byref(gid))
         _check(rc, "mscd_graph_load_csr")
@@ -437,7 +440,8 @@ class Context:
         sp, sdev = _ptr(seeds)
         n_seeds = 0 if seeds is None else int(seeds.shape[0])
         if seeds is not None:
-            assert sdev == dev, "alphas and seeds must both be host or both be device arrays"
+            if sdev != dev:
+                raise ValueError("alphas and seeds must both be host or both be device arrays")
         st = None
         if stream is not None:
             st = stream if isinstance(stream, int) else stream.cuda_stream
