@@ -324,6 +324,36 @@ def test_initial_members_parity(orc, ctx, small_class):
         c.close()
 
 
+@pytest.mark.parametrize("cap", [1, 2])
+def test_round_cap_parity(orc, cap):
+    """The repetition cap: both sides stop every unit after the same number of
+    rounds, report the time-out, and leave the same (partial) communities."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1301_0955_gb300 import mscd
+
+    g = synth.hierarchical_lfr(5000, 20, 200, 2.5, 1.5, (20, 1000), (0.3, 0.1), seed=17)
+    G = oracle_graph(orc, g)
+    alphas = np.array([1.0, 0.7, 0.5, 0.35])
+    seeds = np.arange(0, g.n, 2, dtype=np.int32)
+    rc_o, optr, onodes, of, ost = orc.run(G, alphas, seeds, threads=8, max_rounds=cap)
+    assert rc_o == -8  # some unit needs more rounds than the cap
+    c = mscd.Context(0, max_rounds=cap)
+    try:
+        gid = c.load_csr(g.n, g.row_ptr, g.col)
+        assert c.run(gid, alphas, seeds) == mscd.ETIMEOUT
+        N = len(seeds)
+        for s in range(len(alphas)):
+            ptr, nodes, f, st = c.memberships(s)
+            assert np.array_equal(ptr, optr[s * N:(s + 1) * N + 1] - optr[s * N])
+            assert np.array_equal(nodes, onodes[optr[s * N]:optr[(s + 1) * N]])
+            np.testing.assert_allclose(f, of[s * N:(s + 1) * N], rtol=F_RTOL, atol=0)
+            assert np.array_equal(st[:, :6], ost[s * N:(s + 1) * N, :6])
+    finally:
+        c.close()
+
+
 def structured_graphs():
     """Symmetric graphs where ranking and fitness ties are the rule (the
     smaller-id rule and the strict tests decide most steps; the torus,

@@ -324,6 +324,34 @@ def test_barbell_closed_form(orc, m, alpha):
         assert adds_ok and bridge_fails and no_removal  # the exact case is exercised
 
 
+def test_round_cap(orc):
+    """The repetition cap of Alg. 1 (the paper leaves its value open): a unit
+    that needs R rounds (the last one adds nothing) runs min(R, cap) rounds;
+    with cap >= R - 1 it ends with the uncapped community, and the run reports
+    the time-out whenever some R > cap; units cut before a later growth
+    round end with a different community."""
+    g = synth.hierarchical_lfr(5000, 20, 200, 2.5, 1.5, (20, 1000), (0.3, 0.1), seed=17)
+    G = orc.Graph(g.n, g.row_ptr, g.col)
+    alphas = [1.0, 0.7, 0.5, 0.35]
+    seeds = np.arange(0, g.n, 2, dtype=np.int32)
+    rc, ptr, nodes, f, st = orc.run(G, alphas, seeds, threads=8)
+    assert rc == 0
+    R = st[:, 3]
+    assert R.max() >= 3  # some unit prunes and grows again
+    for cap in (1, 2, int(R.max())):
+        rc2, p2, n2, f2, st2 = orc.run(G, alphas, seeds, threads=8, max_rounds=cap)
+        assert rc2 == (-8 if (R > cap).any() else 0)
+        assert np.array_equal(st2[:, 3], np.minimum(R, cap))
+        cut = 0
+        for u in range(len(R)):
+            same = np.array_equal(nodes[ptr[u]:ptr[u + 1]], n2[p2[u]:p2[u + 1]])
+            if R[u] - 1 <= cap:
+                assert same
+            else:
+                cut += not same
+        assert cut == int((R - 1 > cap).sum())
+
+
 def test_thread_count_independent(orc):
     g0 = synth.config_graph(0)
     g = orc.Graph(g0.n, g0.row_ptr, g0.col)
