@@ -96,3 +96,37 @@ def test_full_method_symmetric_graphs(orc, ctx, name, rule):
     g = SimpleNamespace(n=n, row_ptr=rp, col=col, w=None)
     prio = np.random.default_rng(2).permutation(n).astype(np.int32)
     compare(orc, ctx, g, [1.0, 0.75, 0.5], rule, prio)
+
+
+@pytest.mark.parametrize("max_iters", [1, 3, 7])
+def test_full_method_iteration_cap(orc, ctx, max_iters):
+    """The check-and-merge loop of a scale stopped after max_iters iterations
+    (the 10-cube needs 8 at its first scale): both sides report the time-out,
+    keep that scale's communities as they stand and stop there."""
+    from types import SimpleNamespace
+
+    from paper_1301_0955_gb300 import mscd
+    from test_gpu_parity import structured_graphs
+
+    n, edges = structured_graphs()["hypercube10"]
+    e = np.asarray(edges, np.int64)
+    lo, hi = np.minimum(e[:, 0], e[:, 1]), np.maximum(e[:, 0], e[:, 1])
+    key = np.unique(lo * n + hi)
+    rp, col, _ = synth.to_csr(n, key // n, key % n)
+    g = SimpleNamespace(n=n, row_ptr=rp, col=col, w=None)
+    prio = np.random.default_rng(2).permutation(n).astype(np.int32)
+    alphas = [1.0, 0.75, 0.5]
+    G = orc.Graph(n, rp, col)
+    orc_rc, seeds, out = orc.full(G, alphas, 1, prio, max_iters=max_iters)
+    assert orc_rc == -8 and len(out) == 1
+    gid = ctx.load_csr(n, rp, col)
+    assert ctx.full_run(gid, alphas, prio=prio, seed_rule=1, max_iters=max_iters) == mscd.ETIMEOUT
+    assert np.array_equal(ctx.full_seeds(), seeds)
+    r, o = ctx.full_scale(0), out[0]
+    assert np.array_equal(r["ptr"], o["ptr"]) and np.array_equal(r["nodes"], o["nodes"])
+    assert np.array_equal(r["seeds"], o["seeds"])
+    np.testing.assert_allclose(r["f"], o["f"], rtol=F_RTOL, atol=0)
+    assert r["iterations"] == o["iterations"] == max_iters and r["merges"] == o["merges"]
+    with pytest.raises(mscd.MscdError):
+        ctx.full_scale(1)
+    ctx.free_graph(gid)
