@@ -389,6 +389,15 @@ def test_structured_tie_graphs(orc, ctx, name):
     assert ctx.run(gid, alphas, seeds) == 0
     compare_units(orc, ctx, G, alphas, seeds, threads=8)
     ctx.free_graph(gid)
+    # the same graph with weights from {1/2, 1, 2}: weighted ties stay frequent
+    w = np.random.default_rng(len(name)).choice(np.array([0.5, 1.0, 2.0], np.float32), len(key))
+    rp, col, ww = synth.to_csr(n, key // n, key % n, w)
+    G = orc.Graph(n, rp, col, ww)
+    assert G.status == 0
+    gid = ctx.load_csr(n, rp, col, ww)
+    assert ctx.run(gid, alphas, seeds) == 0
+    compare_units(orc, ctx, G, alphas, seeds, threads=8)
+    ctx.free_graph(gid)
 
 
 def test_hub_node_wide_slots(orc, ctx):
