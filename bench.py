@@ -40,13 +40,15 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_SCALES = 20
+N_SCALES = 20  # the full method's workload (lfr-100k)
 WORKLOAD = ("lfr-100k: 100,000-node LFR-style hierarchical graph (degrees power-law 2.5, mean 20, max 200; "
             "community sizes 20-1000 power-law 1.5; 2 levels, mixing 0.3/0.1; unweighted, seed 1), "
             "20 log-spaced scales in [0.5,1], every node a seed")
 GROW_SOURCES = ["paper_1301_0955_gb300/csrc/grow.cu", "paper_1301_0955_gb300/csrc/exact.cuh",
                 "paper_1301_0955_gb300/csrc/grow.cuh"]
-PROFILE_FILE = os.path.join(ROOT, "profiles", "grow_kernel_lfr100k_traffic.json")
+# DRAM traffic of the growth kernel per workload (ncu capture, see profiles/)
+PROFILE_FILES = {"lfr-100k": os.path.join(ROOT, "profiles", "grow_kernel_lfr100k_traffic.json"),
+                 "lfr-1m-weighted": os.path.join(ROOT, "profiles", "grow_kernel_lfr1m_weighted_traffic.json")}
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -62,11 +64,12 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--seeds", type=int, default=0, help="profiling: a seeded sample of this many seeds")
-    p.add_argument("--scales", type=int, default=N_SCALES, help="profiling: fewer scales")
+    p.add_argument("--scales", type=int, default=0, help="profiling: fewer scales (0: the workload's)")
     p.add_argument("--flush-mib", type=int, default=1024, help="L2 flush buffer written between steps")
     p.add_argument("--plain-steps", type=int, default=1,
                    help="steps of the plain one-launch-per-scale form timed for comparison (0: skip)")
-    p.add_argument("--workload", default="lfr-100k", choices=["lfr-100k", "uneven-batch", "serve", "full", "accuracy"])
+    p.add_argument("--workload", default="lfr-1m-weighted",
+                   choices=["lfr-1m-weighted", "lfr-100k", "uneven-batch", "serve", "full", "accuracy"])
     p.add_argument("--acc-scales", type=int, default=40, help="accuracy: scales in [0.3, 1]")
     p.add_argument("--full-rule", type=int, default=1, help="full: seed rule 1 or 2")
     p.add_argument("--serve-queries", type=int, default=10000, help="serve: queries per load level")
@@ -247,50 +250,59 @@ def oracle_sample_batch(graphs, alphas, seconds, threads):
 
 # ---------------------------------------------------------------- workloads
 
-class Lfr100k:
-    """The 100,000-node LFR-style graph, 20 scales, every node a seed."""
+class SingleGraph:
+    """One resident graph, every scale, every node a seed (or a seeded sample
+    of seeds when profiling)."""
 
-    name = "lfr-100k"
+    name = ""
+    graph_index = 0
+    n_scales_full = 0
+    description = ""
 
-    def __init__(self, args):
-        from paper_1301_0955_gb300 import mscd, synth
+    def __init__(self, args, scales):
+        from paper_1301_0955_gb300 import synth
 
-        self.mscd = mscd
-        self.g = synth.config_graph(1)
-        self.n_scales = args.scales
-        self.alphas = mscd.scales_logspaced(0.5, 1.0, self.n_scales)
+        self.g = synth.config_graph(self.graph_index)
+        self.n_scales = args.scales or self.n_scales_full
+        self.alphas = scales(0.5, 1.0, self.n_scales)
         self.seeds_h = None
         if args.seeds:
             self.seeds_h = np.sort(np.random.default_rng(0).choice(self.g.n, args.seeds,
                                                                    replace=False)).astype(np.int32)
         n_seeds = self.g.n if self.seeds_h is None else len(self.seeds_h)
         self.units = self.n_scales * n_seeds
-        self.full = self.seeds_h is None and self.n_scales == N_SCALES
+        self.full = self.seeds_h is None and self.n_scales == self.n_scales_full
+        self.bytes_per_entry = 4 + (8 if self.g.w is not None else 0)
 
     def config(self):
         g = self.g
-        return {"workload": WORKLOAD if self.full else
-                "profiling subset: %d seeds x %d scales of the lfr-100k workload"
-                % (self.units // self.n_scales, self.n_scales),
-                "n_nodes": g.n, "nnz": g.nnz, "scales": self.n_scales, "seeds": self.units // self.n_scales}
+        return {"workload": self.description if self.full else
+                "profiling subset: %d seeds x %d scales of the %s workload"
+                % (self.units // self.n_scales, self.n_scales, self.name),
+                "n_nodes": g.n, "nnz": g.nnz, "weighted": g.w is not None, "scales": self.n_scales,
+                "seeds": self.units // self.n_scales}
 
     def to_device(self, torch, dev):
-        self.rp_d = torch.from_numpy(self.g.row_ptr).to(dev)
-        self.col_d = torch.from_numpy(self.g.col).to(dev)
+        g = self.g
+        self.rp_d = torch.from_numpy(g.row_ptr).to(dev)
+        self.col_d = torch.from_numpy(g.col).to(dev)
+        self.w_d = None if g.w is None else torch.from_numpy(g.w).to(dev)
         self.alphas_d = torch.from_numpy(self.alphas).to(dev)
         self.seeds_d = None if self.seeds_h is None else torch.from_numpy(self.seeds_h).to(dev)
-        self.rp_h = torch.from_numpy(self.g.row_ptr).pin_memory().numpy()
-        self.col_h = torch.from_numpy(self.g.col).pin_memory().numpy()
-        self.h2d_bytes = int(self.g.row_ptr.nbytes + self.g.col.nbytes + self.alphas.nbytes)
+        self.rp_h = torch.from_numpy(g.row_ptr).pin_memory().numpy()
+        self.col_h = torch.from_numpy(g.col).pin_memory().numpy()
+        self.w_h = None if g.w is None else torch.from_numpy(g.w).pin_memory().numpy()
+        self.h2d_bytes = int(g.row_ptr.nbytes + g.col.nbytes + (0 if g.w is None else g.w.nbytes)
+                             + self.alphas.nbytes + (0 if self.seeds_h is None else self.seeds_h.nbytes))
 
     def step_resident(self, ctx, stream):
-        gid = ctx.load_csr(self.g.n, self.rp_d, self.col_d)
+        gid = ctx.load_csr(self.g.n, self.rp_d, self.col_d, self.w_d)
         rc = ctx.run(gid, self.alphas_d, self.seeds_d, stream=stream)
         require_ok(rc, "mscd_run")
         ctx.free_graph(gid)
 
     def step_e2e(self, ctx):
-        gid = ctx.load_csr(self.g.n, self.rp_h, self.col_h)
+        gid = ctx.load_csr(self.g.n, self.rp_h, self.col_h, self.w_h)
         rc = ctx.run(gid, self.alphas, self.seeds_h)
         require_ok(rc, "mscd_run")
         nb = read_results(ctx, self.n_scales, 1)
@@ -303,24 +315,48 @@ class Lfr100k:
         return oracle_sample(self.g, self.alphas, seconds, threads)
 
 
+class Lfr100k(SingleGraph):
+    """The 100,000-node LFR-style graph, 20 scales, every node a seed."""
+
+    name = "lfr-100k"
+    graph_index = 1
+    n_scales_full = 20
+    description = ("lfr-100k: 100,000-node LFR-style hierarchical graph (degrees power-law 2.5, mean 20, max 200; "
+                   "community sizes 20-1000 power-law 1.5; 2 levels, mixing 0.3/0.1; unweighted, seed 1), "
+                   "20 log-spaced scales in [0.5,1], every node a seed")
+
+
+class Lfr1mWeighted(SingleGraph):
+    """The 1,000,000-node three-level LFR-style graph with FP32 weights, 32
+    scales, every node a seed: 32,000,000 units in one run."""
+
+    name = "lfr-1m-weighted"
+    graph_index = 2
+    n_scales_full = 32
+    description = ("lfr-1m-weighted: 1,000,000-node three-level LFR-style hierarchical graph (degrees power-law "
+                   "2.5, mean 30, max 300; micro community sizes 20-1000 power-law 1.5, grouped 2-6 per level; "
+                   "mixing 0.3/0.2/0.1; FP32 edge weights uniform in [0.5, 2], seed 2), 32 log-spaced scales in "
+                   "[0.5,1], every node a seed, all 32M (scale, seed) units in one persistent run")
+
+
 class UnevenBatch:
     """Many independent graphs of uneven size batched as one disjoint union:
     every seed of every graph at every scale in the same persistent launches."""
 
     name = "uneven-batch"
 
-    def __init__(self, args):
+    def __init__(self, args, scales):
         import multiprocessing as mp
 
-        from paper_1301_0955_gb300 import mscd, synth
+        from paper_1301_0955_gb300 import synth
 
-        self.mscd = mscd
         specs = synth.uneven_batch_specs(args.batch_graphs, seed=4, scale_nodes=args.batch_node_scale)
         # generated on the host cores before any GPU call (spawned workers)
         with mp.get_context("spawn").Pool(min(len(specs), os.cpu_count() or 1)) as pool:
             self.graphs = pool.map(synth.graph_from_spec, specs, chunksize=1)
         self.n_scales = args.batch_scales
-        self.alphas = mscd.scales_logspaced(0.5, 1.0, self.n_scales)
+        self.alphas = scales(0.5, 1.0, self.n_scales)
+        self.bytes_per_entry = 4
         self.n_total = sum(g.n for g in self.graphs)
         self.units = self.n_scales * self.n_total
         self.node_scale = args.batch_node_scale
@@ -373,7 +409,7 @@ class UnevenBatch:
         return oracle_sample_batch(self.graphs, self.alphas, seconds, threads)
 
 
-WORKLOADS = {"lfr-100k": Lfr100k, "uneven-batch": UnevenBatch}
+WORKLOADS = {"lfr-1m-weighted": Lfr1mWeighted, "lfr-100k": Lfr100k, "uneven-batch": UnevenBatch}
 
 
 def percentile(xs, q):
@@ -693,7 +729,14 @@ def run_reference(args):
         print(json.dumps({"impl": "reference", "unavailable": "the reference arm covers the lfr-100k, "
                           "uneven-batch and serve workloads (the oracle on a bounded sample)"}), flush=True)
         return
-    wl = ServeSample(args) if args.workload == "serve" else WORKLOADS[args.workload](args)
+    # the oracle's own scale list: this arm never loads the CUDA library
+    def scales(vmin, a, x):
+        rc, out = oracle.scales_logspaced(vmin, a, x)
+        if rc != 0:
+            raise RuntimeError("orc_scales_logspaced returned %d" % rc)
+        return out
+
+    wl = ServeSample(args) if args.workload == "serve" else WORKLOADS[args.workload](args, scales)
     threads = os.cpu_count() or 1
     per_step = max(1.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
@@ -727,7 +770,11 @@ def main():
         run_accuracy(args)
         return
     world, rank, local = dist_env()
-    wl = WORKLOADS[args.workload](args)  # host-side generation before the first GPU call
+    from paper_1301_0955_gb300 import build, mscd
+
+    build.build()  # nvcc only, no GPU call
+    L = mscd.load()
+    wl = WORKLOADS[args.workload](args, mscd.scales_logspaced)  # host-side generation before the first GPU call
     import torch
 
     if world > 1:
@@ -736,10 +783,6 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_1301_0955_gb300 import build, mscd
-
-    build.build()
-    L = mscd.load()
     ctx = mscd.Context(local)
     stream = torch.cuda.current_stream(dev)
     wl.to_device(torch, dev)
@@ -782,13 +825,18 @@ def main():
     value = whole_job_rate(units, args.steps, world, total_ms)
     st = stats[-1]
     grow_ms = statistics.mean(s["ms_grow"] for s in stats)
-    alg_bytes = 4.0 * st["edges_scanned"] + 16.0 * (st["units"] + st["adds"] + st["removes"])
+    # algorithmic bytes: every scanned CSR entry (column, plus the exact weight
+    # on a weighted graph) and the two row offsets of every row visited
+    alg_bytes = (float(wl.bytes_per_entry) * st["edges_scanned"]
+                 + 16.0 * (st["units"] + st["adds"] + st["removes"]))
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (grow_ms / 1e3) / 1e9
     traffic = None
     try:
-        prof = json.load(open(PROFILE_FILE))
-        if prof.get("source_hash") == source_hash() and prof.get("workload") == wl.name:
+        # only a capture of this kernel source on this exact unit set
+        prof = json.load(open(PROFILE_FILES[wl.name]))
+        if (prof.get("source_hash") == source_hash() and prof.get("workload") == wl.name
+                and prof.get("units") == units):
             traffic = prof.get("dram_bytes_per_step")
     except Exception:
         pass
@@ -812,15 +860,19 @@ def main():
         ctx_p.close()
     e2e = None
     if not args.no_e2e:
-        wl.step_e2e(ctx)  # warm the host path once
-        et, _, _, d2h = timed(lambda c: wl.step_e2e(c), max(1, min(args.steps, 2)), ctx)
+        # the resident warm-up steps already ran every kernel and allocation;
+        # a short workload also warms the host path once
+        step_s = total_ms / args.steps / world / 1e3
+        if step_s < 10.0:
+            wl.step_e2e(ctx)
+        et, _, _, d2h = timed(lambda c: wl.step_e2e(c), 1 if step_s >= 10.0 else max(1, min(args.steps, 2)), ctx)
         e2e = {"value": units / (statistics.mean(et) / 1e3), "unit": "units/s",
                "h2d_bytes_per_step": wl.h2d_bytes, "d2h_bytes_per_step": int(d2h),
                "ms_per_step": statistics.mean(et)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and getattr(wl, "full", True):
         cpu = wl.cpu_baseline(args.cpu_seconds, os.cpu_count() or 1)
-        if wl.name == "lfr-100k":
+        if isinstance(wl, SingleGraph):
             # the same oracle on one host thread, on a smaller adaptive sample
             one = wl.cpu_baseline(max(2.0, args.cpu_seconds / 3), 1)
             cpu["single_thread"] = {"value": one["value"], "unit": one["unit"], "sample": one["sample"]}

@@ -376,7 +376,12 @@ int mscd_grow_noalloc(mscd_ctx *ctx, int32_t graph_id, const double *alphas, int
  * partner in the scan order of Alg. 2 (members ascending); the pairs merge in
  * rounds of disjoint pairs (the partner joins the checked community, which
  * keeps its seed).  The communities at the end of a scale start the next.
- * Every step is deterministic (see the design notes for the order taken).
+ * Every step is deterministic: seeds are chosen in rounds of local minima of
+ * (prio, id), which equals the sequential greedy choice; a community's partner
+ * is the first other community whose shared-node count reaches the ratio,
+ * scanning its members ascending and each member's communities in index
+ * order; a pair joins a merge round if neither side is already in it, and
+ * later pairs rename the absorbed community to its absorber.
  * Host pointers.  ETIMEOUT: a scale needed more than max_iters iterations. */
 typedef struct mscd_full_params {
     int32_t struct_size;  /* sizeof(mscd_full_params)                          */

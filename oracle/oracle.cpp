@@ -21,8 +21,7 @@
 //   * Sec. 4  logarithmic scale sampling and the overlapping NMI of
 //             Lancichinetti, Fortunato & Kertesz averaged over p scales
 //
-// Readings taken where the paper is silent (each is listed in the design
-// notes): k_in counts internal edges twice (internal degree sum); add and
+// Readings taken where the paper is silent or garbled: k_in counts internal edges twice (internal degree sum); add and
 // remove tests are strict; the seed is never removed; priority ties go to
 // the smaller node id; a prune pass walks a snapshot of the members in
 // ascending id and removes at once; the prune loop runs until a pass removes

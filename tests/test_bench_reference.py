@@ -20,8 +20,9 @@ def reference_line(*extra):
     return json.loads(lines[0])
 
 
-@pytest.mark.parametrize("extra", [(), ("--workload", "uneven-batch", "--batch-graphs", "6",
-                                        "--batch-node-scale", "0.03")])
+@pytest.mark.parametrize("extra", [("--workload", "lfr-100k"),
+                                   ("--workload", "uneven-batch", "--batch-graphs", "6",
+                                    "--batch-node-scale", "0.03")])
 def test_reference_arm_line(extra):
     d = reference_line(*extra)
     assert d["impl"] == "reference"
@@ -38,3 +39,19 @@ def test_reference_arm_line(extra):
 def test_reference_arm_unavailable_workload():
     d = reference_line("--workload", "accuracy")
     assert d["impl"] == "reference" and "unavailable" in d
+
+
+def test_reference_arm_never_loads_the_product_library():
+    """The reference arm is the oracle alone: after it has run, no module of
+    the CUDA binding is imported and libmscd.so is not mapped."""
+    code = ("import sys, json; sys.argv = ['bench.py', '--impl', 'reference', '--steps', '1', '--warmup', '3', "
+            "'--cpu-seconds', '1', '--workload', 'lfr-100k']; import bench; bench.main(); "
+            "maps = open('/proc/self/maps').read(); "
+            "print(json.dumps({'mscd_imported': 'paper_1301_0955_gb300.mscd' in sys.modules, "
+            "'libmscd_mapped': 'libmscd' in maps, 'liborc_mapped': 'liborc' in maps}))")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    probe = lines[-1]
+    assert lines[0]["impl"] == "reference"
+    assert probe == {"mscd_imported": False, "libmscd_mapped": False, "liborc_mapped": True}

@@ -175,6 +175,53 @@ def test_scales(orc):
     assert orc.scales_logspaced(-1.0, 1.0, 3)[0] == orc.EINVAL
 
 
+@pytest.mark.parametrize("X,points", [
+    # X a power of 2: log k / log X = j / m at k = 2^j, so the interior values
+    # at those k are the fractions of the way from A down to V_min below
+    (4, {2: (1, 2)}),
+    (8, {2: (1, 3), 4: (2, 3)}),
+    (16, {2: (1, 4), 4: (2, 4), 8: (3, 4)}),
+    (32, {2: (1, 5), 4: (2, 5), 8: (3, 5), 16: (4, 5)}),
+    # X a power of 3
+    (9, {3: (1, 2)}),
+    (27, {3: (1, 3), 9: (2, 3)}),
+    # X = 20 (the benchmark's count): 20 = 4 * 5 gives no rational ratio but
+    # log 4 / log 20 + log 5 / log 20 = 1, i.e. the two offsets from A sum to
+    # A - V_min (checked below)
+])
+def test_scales_interior_closed_form(orc, X, points):
+    """Interior values of the Sec. 4 scale list (read as V_min + (A - V_min)
+    (1 - log k / log X), k = 1..X).  Where log k / log X is the rational j/m,
+    the k-th value is V_min + (A - V_min)(1 - j/m): on [0.5, 1] the k = 2 value
+    of X = 4 is the midpoint 0.75, that of X = 8 is 1 - 0.5/3, and so on.  An
+    off-by-one in k (k - 1, k + 1, 0-based), another logarithm base that is not
+    a ratio, or the garbled (1 - log k) / log X all move these points."""
+    vmin, A = 0.5, 1.0
+    rc, s = orc.scales_logspaced(vmin, A, X)
+    assert rc == 0 and len(s) == X
+    for k, (j, m) in points.items():
+        want = vmin + (A - vmin) * (m - j) / m
+        assert s[k - 1] == pytest.approx(want, rel=0, abs=4e-16), (X, k)
+    # another interval: the same fractions of its width
+    rc, t = orc.scales_logspaced(0.25, 2.0, X)
+    for k, (j, m) in points.items():
+        assert t[k - 1] == pytest.approx(0.25 + 1.75 * (m - j) / m, rel=0, abs=1e-15)
+
+
+def test_scales_interior_complementary_pair(orc):
+    """For X = 20 the ratios at k = 4 and k = 5 sum to one (4 * 5 = 20), so the
+    two values sum to A + V_min; likewise k = 2 and 10, then k = 2 and k = 10
+    against k = 20 (the end, V_min)."""
+    rc, s = orc.scales_logspaced(0.5, 1.0, 20)
+    assert rc == 0
+    assert s[3] + s[4] == pytest.approx(1.5, abs=1e-15)
+    assert s[1] + s[9] == pytest.approx(1.5, abs=1e-15)
+    # X = 32 (the weighted workload's count): k = 2 and k = 16 sum to one
+    rc, t = orc.scales_logspaced(0.5, 1.0, 32)
+    assert t[1] + t[15] == pytest.approx(1.5, abs=1e-15)
+    assert t[3] + t[7] == pytest.approx(1.5, abs=1e-15)
+
+
 def test_window_means(orc):
     nmi = np.array([0.1, 0.2, 0.3, 0.4])  # 5 scales
     w3 = orc.window_means(nmi, 5, 3)
