@@ -185,20 +185,22 @@ __device__ __forceinline__ double log_ratio_fast(i64 a1, i64 a2) {
     return log((double)a1 / (double)a2);
 }
 
-__device__ __noinline__ int sign_slow(i64 a1, i64 a2, i64 b1, i64 b2, double alpha, u32 *flags) {
-    *flags |= EXACT_SLOW;
-    if (is_tie(a1, a2, b1, b2, alpha)) return 0;
+// Stages 3 and 4.  The result is returned by value (the sign plus one, in
+// bits 0-1, and the EXACT_* flags above it) so that no caller state has its
+// address taken by this out-of-line function.
+__device__ __noinline__ u32 sign_slow(i64 a1, i64 a2, i64 b1, i64 b2, double alpha) {
+    const u32 slow = EXACT_SLOW << 2;
+    if (is_tie(a1, a2, b1, b2, alpha)) return slow | 1u;
     dd L1 = log_ratio(a1, a2), L2 = log_ratio(b1, b2);
     dd D = add(L1, neg(mul_d(L2, alpha)));
     double E = 0x1p-92 * (fabs(L1.hi) + alpha * fabs(L2.hi));
-    if (D.hi > E) return 1;
-    if (D.hi < -E) return -1;
-    *flags |= EXACT_UNDECIDED;
-    return 0;
+    if (D.hi > E) return slow | 2u;
+    if (D.hi < -E) return slow | 0u;
+    return slow | (EXACT_UNDECIDED << 2) | 1u;
 }
 
 // Binary64 stage and beyond (integer shortcuts first).
-__device__ __forceinline__ int sign_delta(i64 a1, i64 a2, i64 b1, i64 b2, double alpha, u32 *flags) {
+__device__ __forceinline__ int sign_delta(i64 a1, i64 a2, i64 b1, i64 b2, double alpha, u32 &flags) {
     if (b1 == b2) return (a1 > a2) - (a1 < a2);
     if (a1 == a2) return (b2 > b1) - (b2 < b1);
     double L1 = log_ratio_fast(a1, a2), L2 = log_ratio_fast(b1, b2);
@@ -206,7 +208,9 @@ __device__ __forceinline__ int sign_delta(i64 a1, i64 a2, i64 b1, i64 b2, double
     double E = 0x1p-47 * (fabs(L1) + alpha * fabs(L2));
     if (D > E) return 1;
     if (D < -E) return -1;
-    return sign_slow(a1, a2, b1, b2, alpha, flags);
+    const u32 r = sign_slow(a1, a2, b1, b2, alpha);
+    flags |= r >> 2;
+    return (int)(r & 3u) - 1;
 }
 
 // Binary32 stage in front of sign_delta (GB300 issues binary32 at many times
@@ -229,7 +233,7 @@ __device__ __forceinline__ float log_ratio32(i64 a1, i64 a2) {
 }
 
 __device__ __forceinline__ int sign_delta32(i64 a1, i64 a2, i64 b1, i64 b2, double alpha, float alpha32,
-                                            u32 *flags) {
+                                            u32 &flags) {
     if (b1 == b2) return (a1 > a2) - (a1 < a2);
     if (a1 == a2) return (b2 > b1) - (b2 < b1);
     float L1 = log_ratio32(a1, a2), L2 = log_ratio32(b1, b2);
@@ -241,13 +245,13 @@ __device__ __forceinline__ int sign_delta32(i64 a1, i64 a2, i64 b1, i64 b2, doub
 }
 
 // Add test for a node outside c: (K+2d)/(V+k)^alpha > K/V^alpha.
-__device__ __forceinline__ bool add_test(i64 K, i64 V, i64 d, i64 k, double alpha, float alpha32, u32 *flags) {
+__device__ __forceinline__ bool add_test(i64 K, i64 V, i64 d, i64 k, double alpha, float alpha32, u32 &flags) {
     if (K == 0) return true;  // f_c = 0 < f_{c+n} because d > 0
     return sign_delta32(K + 2 * d, K, V + k, V, alpha, alpha32, flags) > 0;
 }
 
 // Remove test for a member: (K-2d)/(V-k)^alpha > K/V^alpha.
-__device__ __forceinline__ bool remove_test(i64 K, i64 V, i64 d, i64 k, double alpha, float alpha32, u32 *flags) {
+__device__ __forceinline__ bool remove_test(i64 K, i64 V, i64 d, i64 k, double alpha, float alpha32, u32 &flags) {
     if (K == 0 || K - 2 * d == 0) return false;  // f_{c\n} = 0 <= f_c
     return sign_delta32(K - 2 * d, K, V - k, V, alpha, alpha32, flags) > 0;
 }

@@ -37,20 +37,32 @@
 // has a bound, hence a true maximum, below the true maximum minus 2E), so the
 // result is the exact argmax at the cost of a few groups.
 //
-// State per warp: node slots (d_in, k, key, id, flags), group bounds and an
-// open-addressing hash node -> slot, in shared memory (first class) or in a
-// global-memory arena (larger classes, run at high occupancy so that the
-// dependent steps of one unit overlap with those of many others).  A unit
-// whose touched nodes exceed the class capacity stops, is listed, and is
-// grown again in a larger class; the result does not depend on the class or
-// on slot order.
+// State per warp: node slots (d_in, key, id with the member flag in its sign
+// bit; k_u is read from the graph's degree array, which every unit shares),
+// group bounds and an open-addressing hash node -> slot, in shared memory
+// (first class) or in a global-memory arena (larger classes, run at high
+// occupancy so that the dependent steps of one unit overlap with those of
+// many others).  The hash table starts small and doubles (rehashing every
+// slot) whenever it would pass a quarter full, up to twice the slot
+// capacity: a unit's lookups touch a table sized to its own touched nodes,
+// not to its class.  A unit whose touched nodes exceed the class capacity
+// stops, is listed, and is grown again in a larger class; the result does
+// not depend on the class, on the table size or on slot order.
 #include "common.cuh"
 #include "exact.cuh"
 #include "grow.cuh"
 
 namespace {
 
-constexpr unsigned char F_MEMBER = 1u;
+// A slot's id holds the node id (< 2^31) with the member flag in bit 31.
+constexpr i32 MEMBER_BIT = (i32)0x80000000u;
+__device__ __forceinline__ i32 node_of(i32 x) { return x & 0x7fffffff; }
+constexpr int HASH_MIN = 256;  // buckets of a unit's table at its start
+
+// Per-warp counters of the unit being grown (edges scanned, additions,
+// removals), kept in shared memory by the warp's lane 0 rather than in
+// registers of every lane.
+__shared__ unsigned long long g_wcnt[GROW_MAX_THREADS / 32][3];
 
 // Order-preserving int image of a binary32 value (no NaNs occur).
 __device__ __forceinline__ int ord(float f) {
@@ -61,54 +73,56 @@ __device__ __forceinline__ float unord(int o) { return __int_as_float(o >= 0 ? o
 constexpr int ORD_NEG_INF = (int)(0xff800000u ^ 0x7fffffffu);
 constexpr float NEG_INF = -__builtin_huge_valf();
 
-// VT: type of d_in and k in the slots; HT: type of a hash bucket (slot + 1).
+// VT: type of d_in in the slots; HT: type of a hash bucket (slot + 1).
 template <class VT, class HT, bool WEIGHTED>
 struct State {
     VT *din;              // [C] d_in(u, c)
-    VT *kdeg;             // [C] k_u
     float *key;           // [C] ranking key while queued, else -inf
-    i32 *id;              // [C] node id
+    i32 *id;              // [C] node id | MEMBER_BIT for members
+    HT *hsh;              // [Hmax] bucket -> slot + 1 (0 = empty); the first H of the unit in use
+    HT *mem;              // [C] slots of the members, in the order they joined
     int *gmax;            // [C/32] upper bound of the group's largest key (ord image)
     int *qmax;            // [C/32] upper bound of the group's largest d_in / k (ord image)
-    HT *hsh;              // [2C] bucket -> slot + 1 (0 = empty)
-    unsigned char *flag;  // [C]
-    int C, H;
+    const i64 *gk;        // the graph's k_u
+    int C, Hmax;
 };
 
-// Rounded up to 128 bytes: per-warp states are laid end to end, and the
-// 8-byte slot arrays must stay aligned for every warp.
+// Layout: din | key | id | hash | member list | group bounds.  Rounded up to
+// 128 bytes: per-warp states are laid end to end, and the 8-byte slot arrays
+// must stay aligned for every warp; the table starts on a 16-byte boundary
+// (C >= 32).
 template <class VT, class HT, bool WEIGHTED>
 __host__ __device__ __forceinline__ size_t state_bytes_t(int C) {
-    const size_t per = 2 * sizeof(VT) + 4 + 4 + 2 * sizeof(HT) + 1;
+    const size_t per = sizeof(VT) + 4 + 4 + 3 * sizeof(HT);
     const size_t b = (size_t)C * per + 8 * (size_t)(C / 32);
     return (b + 127) & ~(size_t)127;
 }
 
 template <class VT, class HT, bool WEIGHTED>
-__device__ __forceinline__ State<VT, HT, WEIGHTED> carve(unsigned char *base, int C, int *bounds, HT *hsh) {
+__device__ __forceinline__ State<VT, HT, WEIGHTED> carve(unsigned char *base, int C, int *bounds, HT *hsh,
+                                                         const i64 *gk) {
     State<VT, HT, WEIGHTED> s;
     s.C = C;
-    s.H = 2 * C;
+    s.Hmax = 2 * C;
+    s.gk = gk;
     size_t o = 0;
     s.din = (VT *)(base + o);
-    o += sizeof(VT) * (size_t)C;
-    s.kdeg = (VT *)(base + o);
     o += sizeof(VT) * (size_t)C;
     s.key = (float *)(base + o);
     o += 4 * (size_t)C;
     s.id = (i32 *)(base + o);
     o += 4 * (size_t)C;
+    s.hsh = hsh ? hsh : (HT *)(base + o);  // the table may live in shared memory
+    o += 2 * sizeof(HT) * (size_t)C;
+    s.mem = (HT *)(base + o);
+    o += sizeof(HT) * (size_t)C;
     s.gmax = (int *)(base + o);
     o += 4 * (size_t)(C / 32);
     s.qmax = (int *)(base + o);
-    o += 4 * (size_t)(C / 32);
     if (bounds) {  // group bounds kept apart (shared memory for a global-arena class)
         s.gmax = bounds;
         s.qmax = bounds + C / 32;
     }
-    s.hsh = hsh ? hsh : (HT *)(base + o);  // the table may live in shared memory
-    o += 2 * sizeof(HT) * (size_t)C;
-    s.flag = base + o;
     return s;
 }
 
@@ -119,6 +133,10 @@ __device__ __forceinline__ u32 lanemask_lt() {
 }
 
 __device__ __forceinline__ u32 hash_node(i32 v) { return (u32)v * 0x9E3779B1u; }
+
+__device__ __forceinline__ float rank_key(i64 d, i64 k, float alpha32) {
+    return logf(exact::i2f(d)) - alpha32 * logf(exact::i2f(k));
+}
 
 __device__ __forceinline__ u64 mix64(u64 x) {
     x ^= x >> 30;
@@ -132,10 +150,12 @@ __device__ __forceinline__ u64 mix64(u64 x) {
 struct Unit {
     i64 K, V;
     int ns;  // slots in use
+    int nm;  // members (entries of the member list)
+    int H;   // buckets of the hash table in use (a power of two, <= Hmax)
     i32 seed;
     double alpha;
     float alpha32, E2, kmaxf;
-    i64 edges, adds, removes, rounds;
+    i64 rounds;
     u32 xflags;  // EXACT_* of this lane's decisions
     bool ovf;    // slot capacity exceeded
     bool err;    // probe bound hit (cannot happen at load <= 1/2)
@@ -143,47 +163,91 @@ struct Unit {
 
 template <class VT>
 struct SlotView {
-    VT din, kdeg;
-    unsigned char flag;
+    VT din;
+    i64 kdeg;
+    float logk;  // logf of k as a binary32 value (the graph's table)
+    bool member;
 };
+
+// Zero the buckets [0, H) of a table (16-byte stores when the table allows).
+template <class HT>
+__device__ __forceinline__ void zero_table(HT *hsh, int H) {
+    const int lane = threadIdx.x & 31;
+    const size_t bytes = (size_t)H * sizeof(HT);
+    if (((size_t)hsh & 15) == 0 && bytes % 512 == 0) {
+        uint4 *q = (uint4 *)hsh;
+        for (size_t i = lane; i < bytes / 16; i += 32) q[i] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+        for (int i = lane; i < H; i += 32) hsh[i] = 0;
+    }
+}
+
+template <class HT>
+__device__ __forceinline__ HT bucket_cas(HT *p, HT want) {
+    if (sizeof(HT) == 2)
+        return (HT)atomicCAS((unsigned short int *)p, (unsigned short int)0, (unsigned short int)want);
+    return (HT)atomicCAS((unsigned int *)p, 0u, (unsigned int)want);
+}
+
+// Double the unit's table until `incoming` more slots keep it at most a
+// quarter full (or it reaches Hmax), reinserting every slot.  Warp-collective.
+template <class VT, class HT, bool WEIGHTED>
+__device__ void rehash(const State<VT, HT, WEIGHTED> &st, Unit &U, int incoming) {
+    int nH = U.H;
+    while (4 * (U.ns + incoming) > nH && nH < st.Hmax) nH <<= 1;
+    if (nH == U.H) return;
+    __syncwarp();
+    zero_table(st.hsh, U.H);  // buckets at and above U.H are zero already
+    __syncwarp();
+    const u32 hm = (u32)nH - 1u;
+    for (int i = threadIdx.x & 31; i < U.ns; i += 32) {
+        u32 h = hash_node(node_of(st.id[i])) & hm;
+        int p = 0;
+        while (bucket_cas(&st.hsh[h], (HT)(i + 1)) != 0 && ++p < nH) h = (h + 1u) & hm;
+        if (p >= nH) U.err = true;
+    }
+    U.err = __any_sync(FULL_MASK, U.err);
+    U.H = nH;
+    __syncwarp();
+}
 
 // Look up (and insert if absent) node v for every active lane.  Warp-collective.
 template <class VT, class HT, bool WEIGHTED>
 __device__ int lookup_insert(const State<VT, HT, WEIGHTED> &st, const DevGraph &G, Unit &U, i32 v, bool active,
                              SlotView<VT> *sv = nullptr) {
-    const u32 hm = (u32)st.H - 1u;
+    if (4 * (U.ns + 32) > U.H && U.H < st.Hmax) rehash(st, U, 32);
+    const u32 hm = (u32)U.H - 1u;
     int slot = -1;
     u32 h = 0;
     bool need = false;
     if (active) {
+        // k_v is loaded alongside the bucket: both depend only on v
+        if (sv) {
+            sv->kdeg = G.k[v];
+            sv->logk = G.logk[v];
+        }
         h = hash_node(v) & hm;
         int p = 0;
-        for (; p < st.H; ++p) {
+        for (; p < U.H; ++p) {
             const u32 x = st.hsh[h];
             if (x == 0u) {
                 need = true;
                 break;
             }
             const i32 idx = st.id[x - 1];
-            VT dv = 0, kd = 0;
-            unsigned char fl = 0;
-            if (sv) {  // loaded with the id: one dependent step after the bucket
-                dv = st.din[x - 1];
-                kd = st.kdeg[x - 1];
-                fl = st.flag[x - 1];
-            }
-            if (idx == v) {
+            VT dv = 0;
+            if (sv) dv = st.din[x - 1];  // loaded with the id: one dependent step after the bucket
+            if (node_of(idx) == v) {
                 slot = (int)x - 1;
                 if (sv) {
                     sv->din = dv;
-                    sv->kdeg = kd;
-                    sv->flag = fl;
+                    sv->member = idx < 0;
                 }
                 break;
             }
             h = (h + 1u) & hm;
         }
-        if (p == st.H) U.err = true;
+        if (p == U.H) U.err = true;
     }
     const u32 ball = __ballot_sync(FULL_MASK, need);
     if (ball) {
@@ -195,16 +259,12 @@ __device__ int lookup_insert(const State<VT, HT, WEIGHTED> &st, const DevGraph &
         }
         if (need) {
             slot = U.ns + __popc(ball & lanemask_lt());
-            const VT kv = (VT)G.k[v];
             st.id[slot] = v;
             st.din[slot] = 0;
-            st.kdeg[slot] = kv;
             st.key[slot] = NEG_INF;
-            st.flag[slot] = 0;
             if (sv) {
                 sv->din = 0;
-                sv->kdeg = kv;
-                sv->flag = 0;
+                sv->member = false;
             }
         }
         // Claim the empty buckets found.  Only this warp writes its table, so
@@ -226,8 +286,8 @@ __device__ int lookup_insert(const State<VT, HT, WEIGHTED> &st, const DevGraph &
                 do {
                     h = (h + 1u) & hm;
                     ++p;
-                } while (st.hsh[h] != 0 && p < st.H);
-                if (p >= st.H) {
+                } while (st.hsh[h] != 0 && p < U.H);
+                if (p >= U.H) {
                     U.err = true;
                     pending = false;
                 }
@@ -241,10 +301,6 @@ __device__ int lookup_insert(const State<VT, HT, WEIGHTED> &st, const DevGraph &
     return slot;
 }
 
-__device__ __forceinline__ float rank_key(i64 d, i64 k, float alpha32) {
-    return logf(exact::i2f(d)) - alpha32 * logf(exact::i2f(k));
-}
-
 // Slot a ranks before slot b (exact; canonical argument order so that every
 // lane evaluating the pair gets the same answer).
 template <class S>
@@ -254,9 +310,9 @@ __device__ __forceinline__ bool ranks_before(const S &st, int a, float ka, int b
     if (diff < -U.E2) return false;
     const bool swap = a > b;
     const int x = swap ? b : a, y = swap ? a : b;
-    const int s = exact::sign_delta((i64)st.din[x], (i64)st.din[y], (i64)st.kdeg[x], (i64)st.kdeg[y], U.alpha,
-                                    &U.xflags);
-    const bool xfirst = s ? (s > 0) : (st.id[x] < st.id[y]);
+    const i32 ix = node_of(st.id[x]), iy = node_of(st.id[y]);
+    const int s = exact::sign_delta((i64)st.din[x], (i64)st.din[y], st.gk[ix], st.gk[iy], U.alpha, U.xflags);
+    const bool xfirst = s ? (s > 0) : (ix < iy);
     return swap ? !xfirst : xfirst;
 }
 
@@ -326,20 +382,30 @@ __device__ __forceinline__ int max_bound(const S &st, int G) {
     return __reduce_max_sync(FULL_MASK, m);
 }
 
+// Queue = the whole frontier (outside nodes with d_in > 0): every slot's key
+// and every group's two bounds, in one pass.
 template <class S>
-__device__ void rebuild_groups(const S &st, const Unit &U) {
+__device__ void build_queue(const S &st, const Unit &U) {
     const int lane = threadIdx.x & 31;
     const int G = (U.ns + 31) >> 5;
     for (int g = 0; g < G; ++g) {
         const int i = g * 32 + lane;
-        const float k = i < U.ns ? st.key[i] : NEG_INF;
+        float k = NEG_INF, q = NEG_INF;
+        if (i < U.ns) {
+            const i32 x = st.id[i];
+            const i64 d = (i64)st.din[i];
+            if (x >= 0 && d > 0) {
+                const i64 kd = st.gk[x];
+                k = rank_key(d, kd, U.alpha32);
+                q = __fdividef(exact::i2f(d), exact::i2f(kd));
+            }
+            st.key[i] = k;
+        }
         const int o = __reduce_max_sync(FULL_MASK, ord(k));
-        const int q = __reduce_max_sync(
-            FULL_MASK,
-            k == NEG_INF ? ORD_NEG_INF : ord(__fdividef(exact::i2f((i64)st.din[i]), exact::i2f((i64)st.kdeg[i]))));
+        const int qo = __reduce_max_sync(FULL_MASK, k == NEG_INF ? ORD_NEG_INF : ord(q));
         if (lane == 0) {
             st.gmax[g] = o;
-            st.qmax[g] = q;
+            st.qmax[g] = qo;
         }
     }
     for (int g = G + lane; g < st.C / 32; g += 32) {
@@ -420,10 +486,20 @@ __device__ int best_passing(const S &st, Unit &U) {
             ball &= ball - 1;
             const int i = gg * 32 + lane;
             const float k = i < U.ns ? st.key[i] : NEG_INF;
+            i64 d = 0, kd = 1;
+            if (k != NEG_INF) {
+                d = st.din[i];
+                kd = st.gk[node_of(st.id[i])];
+            }
+            // the group's d/k bound made exact again (members and rejected
+            // nodes have left the queue since it was last raised)
+            const int qo =
+                __reduce_max_sync(FULL_MASK, k == NEG_INF ? ORD_NEG_INF
+                                                          : ord(__fdividef(exact::i2f(d), exact::i2f(kd))));
+            if (lane == 0) st.qmax[gg] = qo;
             if (k == NEG_INF) continue;
-            const i64 d = st.din[i], kd = st.kdeg[i];
             if (!exact::add_possible(U.K, U.V, d, kd, U.alpha32)) continue;
-            if (!exact::add_test(U.K, U.V, d, kd, U.alpha, U.alpha32, &U.xflags)) continue;
+            if (!exact::add_test(U.K, U.V, d, kd, U.alpha, U.alpha32, U.xflags)) continue;
             if (best < 0 || ranks_before(st, i, k, best, bk, U)) {
                 best = i;
                 bk = k;
@@ -460,13 +536,35 @@ __device__ void drop_before(const S &st, int best, Unit &U) {
 // Scan the row of the node in `slot`, adding sign*w to d_in of every
 // neighbour; with requeue, (re)insert outside neighbours in the queue with
 // their new key and fold them into their group's best.
+// The first 32 entries of a row, loaded ahead by a caller that expects to
+// expand it (valid = false: nothing loaded).
+struct Chunk {
+    i32 v;
+    i64 w;
+    bool valid;
+};
+
+template <bool WEIGHTED>
+__device__ __forceinline__ Chunk load_chunk(const DevGraph &G, i64 rs, i64 re) {
+    Chunk c;
+    const i64 e = rs + (threadIdx.x & 31);
+    c.v = 0;
+    c.w = 0;
+    if (e < re) {
+        c.v = G.col[e];
+        c.w = WEIGHTED ? G.wfx[e] : 1;
+    }
+    c.valid = true;
+    return c;
+}
+
 template <class VT, class HT, bool WEIGHTED>
 __device__ void expand(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Unit &U, int slot, int sign,
-                       bool requeue, i64 rs = -1, i64 re = -1) {
+                       bool requeue, i64 rs, i64 re, Chunk c0) {
     const DevGraph &G = a.G;
     const int lane = threadIdx.x & 31;
     if (rs < 0) {  // row bounds not loaded by the caller
-        const i32 u = st.id[slot];
+        const i32 u = node_of(st.id[slot]);
         rs = G.rp[u];
         re = G.rp[u + 1];
     }
@@ -475,7 +573,10 @@ __device__ void expand(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Uni
         const bool act = e < re;
         i32 v = 0;
         i64 w = 0;
-        if (act) {
+        if (b == rs && c0.valid) {
+            v = c0.v;
+            w = c0.w;
+        } else if (act) {
             v = G.col[e];
             w = WEIGHTED ? G.wfx[e] : 1;
         }
@@ -488,37 +589,55 @@ __device__ void expand(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Uni
         if (act) {
             d = (i64)sv.din + sign * w;
             st.din[s] = (VT)d;
-            if (requeue && !(sv.flag & F_MEMBER)) {
-                k = rank_key(d, (i64)sv.kdeg, U.alpha32);
+            if (requeue && !sv.member) {
+                k = logf(exact::i2f(d)) - U.alpha32 * sv.logk;  // = rank_key(d, k_v)
                 st.key[s] = k;
                 upd = true;
             }
         }
         if (upd) {
             atomicMax(&st.gmax[s >> 5], ord(k));
-            atomicMax(&st.qmax[s >> 5], ord(__fdividef(exact::i2f(d), exact::i2f((i64)sv.kdeg))));
+            atomicMax(&st.qmax[s >> 5], ord(__fdividef(exact::i2f(d), exact::i2f(sv.kdeg))));
         }
     }
     __syncwarp();
-    U.edges += re - rs;
+    if (lane == 0) g_wcnt[threadIdx.x >> 5][0] += (unsigned long long)(re - rs);
 }
 
 // Add slot s to the community (an addition of the grow pass, or an initial
 // member, which is not counted as one).
+// With c0 valid, the caller also passes gkey, this lane's key of the group of
+// s as it stands (s included): the group's bound is set to the exact largest
+// key left once s leaves the queue, so that the next argmax does not meet a
+// stale bound there.
 template <class VT, class HT, bool WEIGHTED>
-__device__ void accept(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Unit &U, int s, bool counted = true,
-                       i64 rs = -1, i64 re = -1) {
-    const i64 d = st.din[s], kd = st.kdeg[s];
+__device__ void accept(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Unit &U, int s, i32 u, i64 d, i64 kd,
+                       bool counted, i64 rs, i64 re, Chunk c0, float gkey) {
+    const int lane = threadIdx.x & 31;
+    int o = 0;
+    if (c0.valid) o = __reduce_max_sync(FULL_MASK, lane == (s & 31) ? ORD_NEG_INF : ord(gkey));
     __syncwarp();
-    if ((threadIdx.x & 31) == 0) {
-        st.flag[s] |= F_MEMBER;
+    if (lane == 0) {
+        st.id[s] = u | MEMBER_BIT;
         st.key[s] = NEG_INF;
+        st.mem[U.nm] = (HT)s;
+        if (c0.valid) st.gmax[s >> 5] = o;
+        if (counted) g_wcnt[threadIdx.x >> 5][1] += 1ull;
     }
     __syncwarp();
+    U.nm++;
     U.K += 2 * d;
     U.V += kd;
-    if (counted) U.adds++;
-    expand(st, a, U, s, +1, true, rs, re);
+    expand(st, a, U, s, +1, true, rs, re, c0);
+}
+
+template <class VT, class HT, bool WEIGHTED>
+__device__ __forceinline__ void accept_slot(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Unit &U, int s,
+                                            bool counted) {
+    const i32 u = node_of(st.id[s]);
+    Chunk none;
+    none.valid = false;
+    accept(st, a, U, s, u, (i64)st.din[s], st.gk[u], counted, -1, -1, none, NEG_INF);
 }
 
 // Smallest-id member (not the seed, id > last) whose removal raises f; -1 if none.
@@ -527,13 +646,13 @@ __device__ int first_removable(const S &st, Unit &U, i32 last) {
     const int lane = threadIdx.x & 31;
     i32 bid = INT32_MAX;
     int bslot = -1;
-    for (int i = lane; i < U.ns; i += 32) {
-        if (!(st.flag[i] & F_MEMBER)) continue;
-        const i32 u = st.id[i];
+    for (int j = lane; j < U.nm; j += 32) {
+        const int i = st.mem[j];
+        const i32 u = node_of(st.id[i]);
         if (u == U.seed || u <= last || u >= bid) continue;
-        const i64 d = st.din[i], kd = st.kdeg[i];
+        const i64 d = st.din[i], kd = st.gk[u];
         if (!exact::remove_possible(U.K, U.V, d, kd, U.alpha32)) continue;
-        if (!exact::remove_test(U.K, U.V, d, kd, U.alpha, U.alpha32, &U.xflags)) continue;
+        if (!exact::remove_test(U.K, U.V, d, kd, U.alpha, U.alpha32, U.xflags)) continue;
         bid = u;
         bslot = i;
     }
@@ -545,40 +664,42 @@ __device__ int first_removable(const S &st, Unit &U, i32 last) {
 
 template <class VT, class HT, bool WEIGHTED>
 __device__ void remove_node(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, Unit &U, int s) {
-    const i64 d = st.din[s], kd = st.kdeg[s];
+    const int lane = threadIdx.x & 31;
+    const i32 x = st.id[s];
+    const i64 d = st.din[s], kd = st.gk[node_of(x)];
+    // drop s from the member list in place, keeping the others' order: a
+    // lane writes at or below the entry it read, and each chunk is read in
+    // full before it is written
+    int w = 0;
+    for (int b = 0; b < U.nm; b += 32) {
+        const int j = b + lane;
+        const int e = j < U.nm ? (int)st.mem[j] : -1;
+        const bool keep = j < U.nm && e != s;
+        const u32 ball = __ballot_sync(FULL_MASK, keep);
+        __syncwarp();
+        if (keep) st.mem[w + __popc(ball & lanemask_lt())] = (HT)e;
+        w += __popc(ball);
+    }
     __syncwarp();
-    if ((threadIdx.x & 31) == 0) st.flag[s] &= (unsigned char)~F_MEMBER;
+    if (lane == 0) {
+        st.id[s] = node_of(x);
+        g_wcnt[threadIdx.x >> 5][2] += 1ull;
+    }
     __syncwarp();
+    U.nm = w;
     U.K -= 2 * d;
     U.V -= kd;
-    U.removes++;
-    expand(st, a, U, s, -1, false);
+    Chunk none;
+    none.valid = false;
+    expand(st, a, U, s, -1, false, -1, -1, none);
 }
 
-// Empty the hash table for the next unit: first find every slot's bucket
-// (into the key array, no longer needed), then zero them.
+// Empty the hash table for the next unit (only its first U.H buckets were
+// used; the table is sized to the unit, so a plain sweep is short).
 template <class S>
 __device__ void clear_hash(const S &st, const Unit &U) {
-    const int lane = threadIdx.x & 31;
     __syncwarp();
-    if (U.err || 4 * U.ns >= st.H) {
-        for (int i = lane; i < st.H; i += 32) st.hsh[i] = 0;
-    } else {
-        const u32 hm = (u32)st.H - 1u;
-        i32 *pos = (i32 *)st.key;
-        for (int i = lane; i < U.ns; i += 32) {
-            u32 h = hash_node(st.id[i]) & hm;
-            int p = 0;
-            while ((u32)st.hsh[h] != (u32)(i + 1) && p < st.H) {
-                h = (h + 1u) & hm;
-                ++p;
-            }
-            pos[i] = p < st.H ? (i32)h : -1;
-        }
-        __syncwarp();
-        for (int i = lane; i < U.ns; i += 32)
-            if (pos[i] >= 0) st.hsh[pos[i]] = 0;
-    }
+    zero_table(st.hsh, U.err ? st.Hmax : U.H);
     __syncwarp();
 }
 
@@ -588,17 +709,9 @@ template <class S>
 __device__ bool emit(const S &st, const GrowArgs &a, Unit &U, i64 unit, int status) {
     const int lane = threadIdx.x & 31;
     i32 *scr = (i32 *)st.key;
-    int m = 0;
+    const int m = U.nm;
     __syncwarp();
-    for (int b = 0; b < U.ns; b += 32) {
-        const int i = b + lane;
-        const bool mem = i < U.ns && (st.flag[i] & F_MEMBER);
-        const u32 ball = __ballot_sync(FULL_MASK, mem);
-        const i32 v = mem ? st.id[i] : 0;
-        __syncwarp();
-        if (mem) scr[m + __popc(ball & lanemask_lt())] = v;
-        m += __popc(ball);
-    }
+    for (int j = lane; j < m; j += 32) scr[j] = node_of(st.id[st.mem[j]]);
     int P = 1;
     while (P < m) P <<= 1;
     for (int i = m + lane; i < P; i += 32) scr[i] = INT32_MAX;
@@ -644,9 +757,10 @@ __device__ bool emit(const S &st, const GrowArgs &a, Unit &U, i64 unit, int stat
         }
         a.uf[unit] = f;
         i64 *stt = a.ustat + unit * MSCD_NSTATS;
-        stt[MSCD_STAT_EDGES] = U.edges;
-        stt[MSCD_STAT_ADDS] = U.adds;
-        stt[MSCD_STAT_REMOVES] = U.removes;
+        const unsigned long long *wc = g_wcnt[threadIdx.x >> 5];
+        stt[MSCD_STAT_EDGES] = (i64)wc[0];
+        stt[MSCD_STAT_ADDS] = (i64)wc[1];
+        stt[MSCD_STAT_REMOVES] = (i64)wc[2];
         stt[MSCD_STAT_ROUNDS] = U.rounds;
         stt[MSCD_STAT_K] = U.K;
         stt[MSCD_STAT_V] = U.V;
@@ -671,9 +785,13 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
     U.K = 0;
     U.V = G.k[U.seed];
     U.ns = 0;
-    U.edges = U.adds = U.removes = U.rounds = 0;
+    U.nm = 0;
+    U.H = min(HASH_MIN, st.Hmax);
+    U.rounds = 0;
     U.xflags = 0;
     U.ovf = U.err = false;
+    if (lane < 3) g_wcnt[threadIdx.x >> 5][lane] = 0ull;
+    __syncwarp();
     int status = MSCD_OK;
     if (a.big_seed) {
         // this seed's unit outgrew the class at the previous, finer scale: the
@@ -686,9 +804,17 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
     }
 
     lookup_insert(st, G, U, U.seed, lane == 0);  // slot 0
-    if (lane == 0) st.flag[0] = F_MEMBER;
+    if (lane == 0) {
+        st.id[0] = U.seed | MEMBER_BIT;
+        st.mem[0] = 0;
+    }
+    U.nm = 1;
     __syncwarp();
-    expand(st, a, U, 0, +1, false);
+    {
+        Chunk none;
+        none.valid = false;
+        expand(st, a, U, 0, +1, false, -1, -1, none);
+    }
     if (a.init_ptr) {
         // initial members (Alg. 2 may start from given communities); repeats
         // and the seed itself are skipped
@@ -696,8 +822,8 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
             int s = lookup_insert(st, G, U, a.init_nodes[j], lane == 0);
             if (U.ovf || U.err) break;
             s = __shfl_sync(FULL_MASK, s, 0);
-            if (st.flag[s] & F_MEMBER) continue;
-            accept(st, a, U, s, false);
+            if (st.id[s] < 0) continue;  // already a member
+            accept_slot(st, a, U, s, false);
         }
     }
 
@@ -707,31 +833,30 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
             break;
         }
         U.rounds++;
-        // queue = whole frontier
-        for (int i = lane; i < U.ns; i += 32) {
-            const i64 d = st.din[i];
-            st.key[i] =
-                (!(st.flag[i] & F_MEMBER) && d > 0) ? rank_key(d, (i64)st.kdeg[i], U.alpha32) : NEG_INF;
-        }
-        __syncwarp();
-        rebuild_groups(st, U);
+        build_queue(st, U);
         i64 added = 0;
         for (;;) {
             const int top = queue_top(st, U);
             if (top < 0) break;
-            int s = top;
-            // the row of the likely addition, loading during the test
-            const i32 utop = st.id[top];
-            i64 rs = G.rp[utop], re = G.rp[utop + 1];
-            if (!exact::add_test(U.K, U.V, (i64)st.din[top], (i64)st.kdeg[top], U.alpha, U.alpha32, &U.xflags)) {
-                s = best_passing(st, U);
+            const i32 utop = node_of(st.id[top]);
+            const i64 dtop = (i64)st.din[top];
+            const i64 rs = G.rp[utop], re = G.rp[utop + 1];
+            const i64 ktop = st.gk[utop];
+            // loaded during the test, for the likely addition: the first entries
+            // of its row and the keys of its group
+            const int gi = (top & ~31) + lane;
+            const float gkey = gi < U.ns ? st.key[gi] : NEG_INF;
+            const Chunk c0 = load_chunk<WEIGHTED>(G, rs, re);
+            if (exact::add_test(U.K, U.V, dtop, ktop, U.alpha, U.alpha32, U.xflags)) {
+                accept(st, a, U, top, utop, dtop, ktop, true, rs, re, c0, gkey);
+            } else {
+                const int s = best_passing(st, U);
                 // none passes: every queued node is popped and rejected, the grow
                 // pass ends (the next round rebuilds every key)
                 if (s < 0) break;
                 drop_before(st, s, U);
-                rs = -1;
+                accept_slot(st, a, U, s, true);
             }
-            accept(st, a, U, s, true, rs, re);
             added++;
             if (U.ovf || U.err) break;
         }
@@ -742,7 +867,7 @@ __device__ void grow_unit(const State<VT, HT, WEIGHTED> &st, const GrowArgs &a, 
             for (;;) {
                 const int s = first_removable(st, U, last);
                 if (s < 0) break;
-                last = st.id[s];
+                last = node_of(st.id[s]);
                 remove_node(st, a, U, s);
                 removed++;
                 if (U.ovf || U.err) break;
@@ -782,8 +907,8 @@ __global__ void __launch_bounds__(MAXT, MINB) grow_kernel(GrowArgs a) {
     unsigned char *wsm = smem + (size_t)wib * a.smem_per_warp;
     int *bounds = a.bounds_smem ? (int *)wsm : nullptr;
     HT *hsh = a.hash_smem ? (HT *)(wsm + (a.bounds_smem ? 8 * (size_t)(a.cap / 32) : 0)) : nullptr;
-    const State<VT, HT, WEIGHTED> st = carve<VT, HT, WEIGHTED>(base, a.cap, bounds, hsh);
-    for (int i = lane; i < st.H; i += 32) st.hsh[i] = 0;
+    const State<VT, HT, WEIGHTED> st = carve<VT, HT, WEIGHTED>(base, a.cap, bounds, hsh, a.G.k);
+    zero_table(st.hsh, st.Hmax);
     __syncwarp();
     // one call site of grow_unit, and nothing of the plain form live across it
     // (a second inlined copy, or a flag, costs registers)
