@@ -99,6 +99,11 @@ typedef struct mscd_params {
     int32_t hash_smem_slots; /* global-arena classes of at most this many slots keep
                                 their hash table (and group bounds) in shared memory,
                                 the slot arrays in the arena (0 = none)               */
+    int32_t list_hash_bits;  /* testing only: keep this many low bits (1..63) of each
+                                member list's 64-bit hash, so that different lists
+                                share hashes and dedup's exact comparison and
+                                regrouping run on every scale (0 = all 64 bits; the
+                                results are the same either way)                       */
 } mscd_params;
 
 #define MSCD_SCHED_PERSISTENT 0
@@ -346,16 +351,24 @@ const char *mscd_last_error(mscd_ctx *ctx);
  *              out_offset[u], length out_len[u]), out_fitness double[U],
  *              out_stats int64[U*MSCD_NSTATS], out_status int32[U],
  *              out_hash uint64[U] (hash of each member list)
- *   *n_nodes_needed  total member-list length of all units (host)
+ *   *n_nodes_needed  total member-list length of all units (host); set on
+ *              MSCD_OK and MSCD_ESMALL only (after MSCD_ERANGE it leaves out
+ *              the units that did not finish)
  *   cuda_stream      stream to order the work on (NULL = default stream)
- * Limits and errors: at most 2^20 units per call and 8192 touched nodes per
- * unit (MSCD_ERANGE when a unit needs more); MSCD_ESMALL when out_cap <
- * *n_nodes_needed; MSCD_EINVAL for bad arguments or seeds.  The first call
- * on a device looks up the array's device address once (make that first call
- * before any stream capture).  Every call reuses the same array, which keeps
- * the previous call's contents (the call clears what must start at zero):
- * calls that overlap on the GPU, on any stream or context of one device,
- * race on it and must not be issued. */
+ * Limits and errors: MSCD_ERANGE for more than 2^20 units or 256 scales in
+ * one call, and for a unit that touches more than 8192 nodes (the per-unit
+ * slot arena of the array); MSCD_ESMALL when out_cap < *n_nodes_needed;
+ * MSCD_EINVAL for bad arguments or seeds.  The array holds the states of
+ * about 270 (weighted graphs) to 380 (unweighted) units at once, so a call
+ * keeps a fraction of a large GPU busy: it suits small and medium batches.
+ * The call waits for its stream (cudaStreamSynchronize) after the seed check,
+ * when seeds are given, and once more to read its counters back; it returns
+ * with the outputs written.  The first call on a device looks up the array's
+ * device address once (make that first call before any stream capture).
+ * Every call reuses the same array, which keeps the previous call's contents
+ * (the call clears what must start at zero): calls that overlap on the GPU,
+ * on any stream or context of one device, race on it and must not be
+ * issued. */
 int mscd_grow_noalloc(mscd_ctx *ctx, int32_t graph_id, const double *alphas, int32_t n_scales,
                       const int32_t *seeds, int64_t n_seeds, int32_t *out_nodes, int64_t out_cap,
                       int64_t *out_offset, int32_t *out_len, double *out_fitness, int64_t *out_stats,
@@ -440,6 +453,12 @@ typedef struct mscd_serve_stats {
     int64_t in_flight_bytes;      /* held by running batches now                  */
     int64_t max_in_flight_bytes;  /* largest holding seen                         */
     int64_t budget_bytes;
+    int64_t max_concurrent_batches; /* most completed batches whose device
+                                       intervals (first copy in to last copy
+                                       out, timed by CUDA events on the
+                                       worker's stream) overlapped at once   */
+    int64_t overlap_us;           /* device time with two or more batches in
+                                     flight, microseconds                     */
 } mscd_serve_stats;
 
 #define MSCD_Q_QUEUED 0
@@ -457,6 +476,13 @@ int mscd_serve_stop(mscd_ctx *ctx);
  * resident graph graph_id at scale alpha (finite, > 0).  *qid names it. */
 int mscd_query_submit(mscd_ctx *ctx, int32_t graph_id, const int32_t *seeds, int32_t n_seeds, double alpha,
                       uint64_t *qid);
+
+/* Device intervals of the completed batches, in completion order:
+ * start_ms[i] and end_ms[i] (host double[cap]) are milliseconds after the
+ * server started, from the batch's first host->device copy to its last
+ * device->host copy, as CUDA events on the worker's stream timed them.
+ * ESMALL with *n when cap is short. */
+int mscd_serve_batch_intervals(mscd_ctx *ctx, double *start_ms, double *end_ms, int64_t cap, int64_t *n);
 
 /* State of a query (MSCD_Q_*); wait: until done or timeout_us passed. */
 int mscd_query_poll(mscd_ctx *ctx, uint64_t qid, int32_t *state);

@@ -738,6 +738,78 @@ extern "C" double orc_nmi(i64 n, i64 cx, const i64 *xp, const i32 *xn, i64 cy, c
     return 1.0 - 0.5 * (hxy + hyx);
 }
 
+// The same definition for covers too large for the pairwise list
+// intersections above (tens of thousands of communities of hundreds of
+// nodes).  Only the intersection sizes are obtained differently: n11 of
+// (X_k, Y_l) is counted over the members of X_k and, for each, the Y
+// communities holding it (a node -> communities index of Y); every other
+// pair has n11 = 0.  Each pair is then evaluated by the same formulas, h()
+// read from a table of hlog(c, n) for c = 0..n (the same values), the
+// minimum over l is taken, and the per-k terms are summed in k order, so the
+// result is the one cond_entropy_norm gives.  Threads split the k range.
+static double cond_entropy_norm_indexed(i64 n, i64 cx, const i64 *xp, const i32 *xn, i64 cy, const i64 *yp,
+                                        const i32 *yn, int n_threads) {
+    std::vector<double> T(n + 1);
+    for (i64 c = 0; c <= n; c++) T[c] = hlog(c, n);
+    // node -> Y communities
+    std::vector<i64> np(n + 1, 0);
+    for (i64 l = 0; l < cy; l++)
+        for (i64 j = yp[l]; j < yp[l + 1]; j++) np[yn[j] + 1]++;
+    for (i64 v = 0; v < n; v++) np[v + 1] += np[v];
+    std::vector<i64> nl(np[n]);
+    {
+        std::vector<i64> fill(np.begin(), np.end() - 1);
+        for (i64 l = 0; l < cy; l++)
+            for (i64 j = yp[l]; j < yp[l + 1]; j++) nl[fill[yn[j]]++] = l;
+    }
+    std::vector<double> term(cx);
+    auto work = [&](i64 k0, i64 k1) {
+        std::vector<i64> cnt(cy, 0);
+        std::vector<i64> touched;
+        for (i64 k = k0; k < k1; k++) {
+            const i64 sx = xp[k + 1] - xp[k];
+            const double Hx = T[sx] + T[n - sx];
+            double best = Hx;
+            touched.clear();
+            for (i64 j = xp[k]; j < xp[k + 1]; j++) {
+                const i32 v = xn[j];
+                for (i64 q = np[v]; q < np[v + 1]; q++) {
+                    if (cnt[nl[q]]++ == 0) touched.push_back(nl[q]);
+                }
+            }
+            for (i64 l = 0; l < cy; l++) {
+                const i64 sy = yp[l + 1] - yp[l];
+                const i64 n11 = cnt[l];
+                const i64 n10 = sx - n11, n01 = sy - n11, n00 = n - n11 - n10 - n01;
+                const i64 lo1 = std::min(n11, n00), hi1 = std::max(n11, n00);
+                const i64 lo2 = std::min(n01, n10), hi2 = std::max(n01, n10);
+                if (lo1 == lo2 && hi1 == hi2) continue;
+                if (!(T[n11] + T[n00] > T[n01] + T[n10])) continue;
+                const double Hxy = T[n11] + T[n10] + T[n01] + T[n00];
+                const double Hy = T[sy] + T[n - sy];
+                best = std::min(best, Hxy - Hy);
+            }
+            for (i64 l : touched) cnt[l] = 0;
+            term[k] = (Hx > 0.0) ? best / Hx : 0.0;
+        }
+    };
+    const int t = std::max(1, n_threads);
+    std::vector<std::thread> th;
+    for (int i = 0; i < t; i++) th.emplace_back(work, cx * i / t, cx * (i + 1) / t);
+    for (auto &x : th) x.join();
+    double total = 0.0;
+    for (i64 k = 0; k < cx; k++) total += term[k];
+    return total / (double)cx;
+}
+
+extern "C" double orc_nmi_indexed(i64 n, i64 cx, const i64 *xp, const i32 *xn, i64 cy, const i64 *yp,
+                                  const i32 *yn, int n_threads) {
+    if (cx <= 0 || cy <= 0 || n <= 0) return NAN;
+    double hxy = cond_entropy_norm_indexed(n, cx, xp, xn, cy, yp, yn, n_threads);
+    double hyx = cond_entropy_norm_indexed(n, cy, yp, yn, cx, xp, xn, n_threads);
+    return 1.0 - 0.5 * (hxy + hyx);
+}
+
 // Mean of the successive-scale NMI values inside a window of p scales centred
 // on each scale i (scales i - (p-1)/2 ... i + p-1 - (p-1)/2, clipped to the
 // list).  nmi has S-1 entries (nmi[j] compares scales j and j+1).

@@ -291,7 +291,8 @@ int mscd_create(mscd_ctx **out, int device, const mscd_params *params) {
     if (c->p.smem_slots < 0) c->p.smem_slots = 0;
     if (c->p.mid_slots < 0) c->p.mid_slots = 0;
     if (c->p.global_warps_per_sm <= 0) c->p.global_warps_per_sm = 16;
-    if (c->p.global_slots < 0 || (c->p.global_slots & (c->p.global_slots - 1)) ||
+    if (c->p.list_hash_bits < 0 || c->p.list_hash_bits > 63 || c->p.global_slots < 0 ||
+        (c->p.global_slots & (c->p.global_slots - 1)) ||
         (c->p.schedule != MSCD_SCHED_PERSISTENT && c->p.schedule != MSCD_SCHED_PER_SCALE)) {
         delete c;
         return MSCD_EINVAL;
@@ -584,6 +585,7 @@ int run_impl(mscd_ctx *c, int32_t graph_id, const double *alphas, int32_t n_scal
         proto.init_ptr = c->init_ptr;
         proto.init_nodes = c->init_nodes;
         proto.log_kmax = G.kmax > 1 ? (float)std::log((double)G.kmax) : 0.0f;
+        proto.hash_clear = c->p.list_hash_bits > 0 ? ~(((u64)1 << c->p.list_hash_bits) - 1) : 0;
         c->pipe.p = c->p;
         c->pipe.st = st;
         c->pipe.stats = &c->stats;

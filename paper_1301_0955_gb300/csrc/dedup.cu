@@ -6,7 +6,7 @@
 // hash table; the representative of a group is its smallest unit (= seed)
 // index; every unit's list is compared element by element with its
 // representative's, and the rare unit whose list differs despite an equal
-// hash is regrouped exactly by a plain pairwise pass.  Unique communities are
+// hash is regrouped exactly by a warp-parallel pass over those units.  Unique communities are
 // numbered in order of their representative (smallest generating seed index).
 #include <algorithm>
 
@@ -59,25 +59,57 @@ __global__ void verify(const i64 *uoff, const i32 *ulen, const i32 *nodes, const
     }
 }
 
-// Plain pairwise regrouping of the units whose list differed from their
-// hash group's representative (equal lists have equal hashes, so every such
-// group lies entirely inside this set).  Single thread; expected never to run.
-__global__ void regroup_collisions(const i64 *uoff, const i32 *ulen, const i32 *nodes, i64 N, i64 *urep) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (i64 u = 0; u < N; ++u) {
-        if (urep[u] != -1) continue;
-        urep[u] = u;
-        for (i64 v = 0; v < u; ++v) {
-            if (urep[v] != v || ulen[v] != ulen[u]) continue;
-            // v is a regrouped representative only if it was itself a collision
-            const i32 *a = nodes + uoff[u], *b = nodes + uoff[v];
-            bool eq = true;
-            for (int i = 0; i < ulen[u] && eq; ++i) eq = a[i] == b[i];
-            if (eq) {
-                urep[u] = v;
-                break;
+// Exact regrouping of the units whose list differed from their hash group's
+// representative (equal lists have equal hashes, so every equal-list class
+// of such units lies inside this set).  The set is listed in ascending unit
+// order; a warp per listed unit finds the first listed unit with the same
+// hash, length and list (itself at the latest), which is the smallest unit of
+// its class: every class gets its smallest unit as representative, as the
+// sequential pairwise pass would.
+__global__ void flag_collisions(const i64 *urep, i64 N, i64 *flag) {
+    for (i64 u = (i64)blockIdx.x * blockDim.x + threadIdx.x; u < N; u += (i64)gridDim.x * blockDim.x)
+        flag[u] = urep[u] == -1 ? 1 : 0;
+}
+
+__global__ void list_collisions(const i64 *flag, const i64 *pos, i64 N, i64 *list) {
+    for (i64 u = (i64)blockIdx.x * blockDim.x + threadIdx.x; u < N; u += (i64)gridDim.x * blockDim.x)
+        if (flag[u]) list[pos[u]] = u;
+}
+
+__global__ void regroup_collisions(const i64 *list, const i64 *n_list, const u64 *uhash, const i64 *uoff,
+                                   const i32 *ulen, const i32 *nodes, i64 *urep) {
+    const int lane = threadIdx.x & 31;
+    const i64 X = *n_list;
+    const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
+    for (i64 j = (i64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < X; j += warps) {
+        const i64 u = list[j];
+        const u64 hu = uhash[u];
+        const i32 lu = ulen[u];
+        const i32 *a = nodes + uoff[u];
+        i64 rep = u;
+        for (i64 b = 0; b < j; b += 32) {
+            // candidates of this chunk with the same hash and length, then each
+            // compared in ascending order until one equals
+            const i64 i = b + lane;
+            const i64 v = i < j ? list[i] : -1;
+            u32 cand = __ballot_sync(FULL_MASK, v >= 0 && uhash[v] == hu && ulen[v] == lu);
+            bool found = false;
+            while (cand) {
+                const int l = __ffs(cand) - 1;
+                cand &= cand - 1;
+                const i64 w = __shfl_sync(FULL_MASK, v, l);
+                const i32 *c = nodes + uoff[w];
+                bool diff = false;
+                for (i32 k = lane; k < lu; k += 32) diff |= a[k] != c[k];
+                if (!__any_sync(FULL_MASK, diff)) {
+                    rep = w;
+                    found = true;
+                    break;
+                }
             }
+            if (found) break;
         }
+        if (lane == 0) urep[u] = rep;
     }
 }
 
@@ -163,7 +195,14 @@ int dedup_scale(const i64 *uoff, const i32 *ulen, const u64 *uhash, const double
         if ((rc = cuda_status(cudaMemcpyAsync(&h_err, err, sizeof(h_err), cudaMemcpyDeviceToHost, st)))) break;
         if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
         if (h_err) { rc = MSCD_EDEVICE; break; }
-        if (h_coll) { regroup_collisions<<<1, 32, 0, st>>>(uoff, ulen, nodes, N, urep); note_launch(); }
+        if (h_coll) {
+            // flag is reused below (mark_reps overwrites it); cid holds the positions
+            flag_collisions<<<blocks, 256, 0, st>>>(urep, N, flag); note_launch();
+            if ((rc = scan_exclusive_i64(flag, cid, N, tot, st))) break;
+            list_collisions<<<blocks, 256, 0, st>>>(flag, cid, N, uent); note_launch();  // uent is free now
+            const unsigned rblocks = (unsigned)std::max<u64>(1, std::min<u64>((h_coll + 7) / 8, 152 * 16));
+            regroup_collisions<<<rblocks, 256, 0, st>>>(uent, tot, uhash, uoff, ulen, nodes, urep); note_launch();
+        }
         mark_reps<<<blocks, 256, 0, st>>>(urep, N, flag); note_launch();
         if ((rc = scan_exclusive_i64(flag, cid, N, tot, st))) break;
         i64 C = 0;

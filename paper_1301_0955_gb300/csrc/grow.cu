@@ -512,7 +512,7 @@ __device__ int best_passing(const S &st, Unit &U) {
 
 // Pop (reject) every queued slot ranked before `best`.  Such a slot has a key
 // above key(best) - E2, so only groups whose bound reaches key(best) - 2 E2
-// are visited.  Group bounds stay upper bounds.
+// are visited; their bounds are recomputed, the others stay upper bounds.
 template <class S>
 __device__ void drop_before(const S &st, int best, Unit &U) {
     const int lane = threadIdx.x & 31;
@@ -527,7 +527,11 @@ __device__ void drop_before(const S &st, int best, Unit &U) {
             ball &= ball - 1;
             const int i = gg * 32 + lane;
             const float k = i < U.ns ? st.key[i] : NEG_INF;
-            if (k != NEG_INF && ranks_before(st, i, k, best, bk, U)) st.key[i] = NEG_INF;
+            const bool drop = k != NEG_INF && ranks_before(st, i, k, best, bk, U);
+            if (drop) st.key[i] = NEG_INF;
+            // the group's key bound made exact again
+            const int o = __reduce_max_sync(FULL_MASK, drop ? ORD_NEG_INF : ord(k));
+            if (lane == 0) st.gmax[gg] = o;
         }
     }
     __syncwarp();
@@ -737,6 +741,7 @@ __device__ bool emit(const S &st, const GrowArgs &a, Unit &U, i64 unit, int stat
 #pragma unroll
     for (int o = 16; o; o >>= 1) h += __shfl_xor_sync(FULL_MASK, h, o);
     h ^= mix64((u64)m);
+    h &= ~a.hash_clear;
     if (h == 0) h = 1;
     unsigned long long off = 0;
     if (lane == 0) off = atomicAdd(a.out_cursor, (unsigned long long)m);

@@ -45,6 +45,7 @@ struct GrowArgs {
     i64 *uoff;
     i32 *ulen;
     u64 *uhash;
+    u64 hash_clear;         // bits cleared in every list hash (0; set only by tests of the collision path)
     double *uf;
     i64 *ustat;
     i32 *ustatus;

@@ -81,6 +81,7 @@ struct Worker {
     i32 *h_status = nullptr;
     i32 *h_nodes = nullptr;
     i64 h_nodes_cap = 0;
+    cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // device interval of the batch in flight
     std::thread th;
 };
 
@@ -100,6 +101,9 @@ void free_worker(Worker &w) {
     cudaFreeHost(w.h_uf);
     cudaFreeHost(w.h_status);
     cudaFreeHost(w.h_nodes);
+    if (w.ev_start) cudaEventDestroy(w.ev_start);
+    if (w.ev_end) cudaEventDestroy(w.ev_end);
+    w.ev_start = w.ev_end = nullptr;
     pipe_free(w.pipe);
     if (w.pipe.st) cudaStreamDestroy(w.pipe.st);
     w.pipe.st = nullptr;
@@ -122,6 +126,8 @@ int alloc_worker(Worker &w, i64 cap) {
     MSCD_CUDA(cudaMallocHost((void **)&w.h_uf, cap * sizeof(double)));
     MSCD_CUDA(cudaMallocHost((void **)&w.h_status, cap * sizeof(i32)));
     MSCD_CUDA(cudaStreamCreateWithFlags(&w.pipe.st, cudaStreamNonBlocking));
+    MSCD_CUDA(cudaEventCreate(&w.ev_start));
+    MSCD_CUDA(cudaEventCreate(&w.ev_end));
     return pipe_reserve(w.pipe, cap);
 }
 
@@ -141,6 +147,11 @@ struct Server {
     bool stopping = false;
     std::vector<std::unique_ptr<Worker>> workers;
     mscd_serve_stats stats{};
+    // Device intervals of completed batches, in milliseconds after `ref`, an
+    // event recorded when the server started: [start, end) from the batch's
+    // first copy to its last, as the GPU timed them on the worker's stream.
+    cudaEvent_t ref = nullptr;
+    std::vector<std::pair<double, double>> intervals;
 
     // expected bytes of a query while it runs
     i64 estimate(const Query &q) {
@@ -170,6 +181,7 @@ int Server::grow_batch(Worker *w, std::vector<Query *> &batch) {
         n += (i64)q->seeds.size();
     }
     cudaStream_t st = w->pipe.st;
+    MSCD_CUDA(cudaEventRecord(w->ev_start, st));
     MSCD_CUDA(cudaMemcpyAsync(w->seeds, w->h_seeds, n * sizeof(i32), cudaMemcpyHostToDevice, st));
     MSCD_CUDA(cudaMemcpyAsync(w->alpha, w->h_alpha, n * sizeof(double), cudaMemcpyHostToDevice, st));
     std::vector<int> ladder;
@@ -208,7 +220,16 @@ int Server::grow_batch(Worker *w, std::vector<Query *> &batch) {
     MSCD_CUDA(cudaMemcpyAsync(w->h_status, w->ustatus, n * sizeof(i32), cudaMemcpyDeviceToHost, st));
     if (total > 0)
         MSCD_CUDA(cudaMemcpyAsync(w->h_nodes, w->pipe.out_nodes, total * sizeof(i32), cudaMemcpyDeviceToHost, st));
+    MSCD_CUDA(cudaEventRecord(w->ev_end, st));
     MSCD_CUDA(cudaStreamSynchronize(st));
+    {
+        float t0 = 0.0f, t1 = 0.0f;
+        if (cudaEventElapsedTime(&t0, ref, w->ev_start) == cudaSuccess &&
+            cudaEventElapsedTime(&t1, ref, w->ev_end) == cudaSuccess) {
+            std::lock_guard<std::mutex> lk(m);
+            intervals.push_back({(double)t0, (double)t1});
+        }
+    }
     // split per query: lists in seed order
     i64 u = 0;
     for (Query *q : batch) {
@@ -317,6 +338,7 @@ void serve_destroy(Server *s) {
         if (w->th.joinable()) w->th.join();
     cudaSetDevice(s->device);
     for (auto &w : s->workers) free_worker(*w);
+    if (s->ref) cudaEventDestroy(s->ref);
     delete s;
 }
 
@@ -364,6 +386,15 @@ int mscd_serve_start(mscd_ctx *c, const mscd_serve_params *params) {
     }
     if (rc) {
         for (auto &w : s->workers) free_worker(*w);
+        delete s;
+        return rc;
+    }
+    if (rc == MSCD_OK) rc = cuda_status(cudaEventCreate(&s->ref));
+    if (rc == MSCD_OK) rc = cuda_status(cudaEventRecord(s->ref, s->workers[0]->pipe.st));
+    if (rc == MSCD_OK) rc = cuda_status(cudaEventSynchronize(s->ref));
+    if (rc) {
+        for (auto &w : s->workers) free_worker(*w);
+        if (s->ref) cudaEventDestroy(s->ref);
         delete s;
         return rc;
     }
@@ -481,6 +512,38 @@ int mscd_serve_get_stats(mscd_ctx *c, mscd_serve_stats *out) {
     out->queued = (i64)s->pending.size();
     out->in_flight_bytes = s->in_use;
     out->budget_bytes = s->budget;
+    // sweep over the batches' device intervals: ends before starts at equal times
+    std::vector<std::pair<double, int>> ev;
+    ev.reserve(2 * s->intervals.size());
+    for (const auto &iv : s->intervals) {
+        ev.push_back({iv.first, +1});
+        ev.push_back({iv.second, -1});
+    }
+    std::sort(ev.begin(), ev.end());
+    i64 cur = 0, best = 0;
+    double overlap = 0.0, last = 0.0;
+    for (const auto &e : ev) {
+        if (cur >= 2) overlap += e.first - last;
+        cur += e.second;
+        last = e.first;
+        best = std::max(best, cur);
+    }
+    out->max_concurrent_batches = best;
+    out->overlap_us = (i64)(overlap * 1000.0);
+    return MSCD_OK;
+}
+
+int mscd_serve_batch_intervals(mscd_ctx *c, double *start_ms, double *end_ms, int64_t cap, int64_t *n) {
+    if (!c || !n) return MSCD_EINVAL;
+    Server *s = *ctx_server(c);
+    if (!s) return MSCD_EINVAL;
+    std::lock_guard<std::mutex> lk(s->m);
+    *n = (i64)s->intervals.size();
+    if (cap < *n || (*n > 0 && (!start_ms || !end_ms))) return MSCD_ESMALL;
+    for (i64 i = 0; i < *n; ++i) {
+        start_ms[i] = s->intervals[i].first;
+        end_ms[i] = s->intervals[i].second;
+    }
     return MSCD_OK;
 }
 

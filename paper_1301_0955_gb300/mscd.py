@@ -38,7 +38,7 @@ class mscd_params(C.Structure):
     _fields_ = [("struct_size", C.c_int32), ("warps_per_block", C.c_int32), ("smem_slots", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("mid_slots", C.c_int32), ("global_warps_per_sm", C.c_int32),
                 ("global_slots", C.c_int32), ("max_rounds", C.c_int64), ("schedule", C.c_int32),
-                ("hash_smem_slots", C.c_int32)]
+                ("hash_smem_slots", C.c_int32), ("list_hash_bits", C.c_int32)]
 
 
 class mscd_serve_params(C.Structure):
@@ -48,7 +48,8 @@ class mscd_serve_params(C.Structure):
 
 class mscd_serve_stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("queries_submitted", "queries_done", "units_done", "batches", "queued",
-                                         "in_flight_bytes", "max_in_flight_bytes", "budget_bytes")]
+                                         "in_flight_bytes", "max_in_flight_bytes", "budget_bytes",
+                                         "max_concurrent_batches", "overlap_us")]
 
 
 class mscd_full_params(C.Structure):
@@ -108,6 +109,7 @@ SIGNATURES = {
     "mscd_query_wait": (C.c_int, [vp, C.c_uint64, C.c_int64, i32p]),
     "mscd_query_result": (C.c_int, [vp, C.c_uint64, i64p, i32p, C.c_int64, f64p, i64p, f64p]),
     "mscd_serve_get_stats": (C.c_int, [vp, C.POINTER(mscd_serve_stats)]),
+    "mscd_serve_batch_intervals": (C.c_int, [vp, f64p, f64p, C.c_int64, i64p]),
     "mscd_graph_union": (C.c_int, [vp, i32p, C.c_int32, i32p]),
     "mscd_graph_parts": (C.c_int, [vp, C.c_int32, i64p, C.c_int32, i32p]),
     "mscd_get_run_stats": (C.c_int, [vp, C.POINTER(mscd_run_stats)]),
@@ -236,10 +238,10 @@ class Context:
 
     def __init__(self, device: int = 0, smem_slots: int = 0, blocks_per_sm: int = 0, max_rounds: int = 0,
                  warps_per_block: int = 0, mid_slots: int = 0, global_warps_per_sm: int = 0,
-                 global_slots: int = 0, schedule: int = 0, hash_smem_slots: int = 0):
+                 global_slots: int = 0, schedule: int = 0, hash_smem_slots: int = 0, list_hash_bits: int = 0):
         L = load()
         p = mscd_params(C.sizeof(mscd_params), warps_per_block, smem_slots, blocks_per_sm, mid_slots,
-                        global_warps_per_sm, global_slots, max_rounds, schedule, hash_smem_slots)
+                        global_warps_per_sm, global_slots, max_rounds, schedule, hash_smem_slots, list_hash_bits)
         h = vp()
         _check(L.mscd_create(C.byref(h), device, C.byref(p)), "mscd_create")
         self.h = h
@@ -398,6 +400,21 @@ class Context:
         _check(load().mscd_serve_get_stats(self.h, C.byref(st)), "mscd_serve_get_stats")
         return {k: getattr(st, k) for k, _ in mscd_serve_stats._fields_}
 
+    def batch_intervals(self):
+        """(start_ms, end_ms) device intervals of the completed serving batches."""
+        n = C.c_int64()
+        rc = load().mscd_serve_batch_intervals(self.h, None, None, 0, C.byref(n))
+        if rc not in (OK, ESMALL):
+            _check(rc, "mscd_serve_batch_intervals")
+        a = np.zeros(max(n.value, 1), np.float64)
+        b = np.zeros(max(n.value, 1), np.float64)
+        rc = load().mscd_serve_batch_intervals(self.h, a.ctypes.data_as(f64p), b.ctypes.data_as(f64p), len(a),
+                                               C.byref(n))
+        if rc not in (OK, ESMALL):  # batches may have completed in between
+            _check(rc, "mscd_serve_batch_intervals")
+        m = min(n.value, len(a))
+        return a[:m], b[:m]
+
     def graph_union(self, gids) -> int:
         """Disjoint union of resident graphs as one resident graph (batching)."""
         ids = np.ascontiguousarray(gids, np.int32)
@@ -495,6 +512,20 @@ class Context:
                                            stt.ctypes.data_as(i64p) if with_stats else None, C.byref(tot)),
                "mscd_get_memberships")
         return ptr, nodes[: tot.value], f[:N], stt[:N]
+
+    def unit_stats(self, scale: int):
+        """(fitness[n_seeds], stats[n_seeds, 8]) of every unit of a scale,
+        without copying the member lists (mscd_get_memberships with no node
+        buffer)."""
+        N = self.n_seeds
+        f = np.zeros(max(N, 1), np.float64)
+        stt = np.zeros((max(N, 1), NSTATS), np.int64)
+        tot = C.c_int64()
+        rc = load().mscd_get_memberships(self.h, scale, None, None, 0, f.ctypes.data_as(f64p),
+                                         stt.ctypes.data_as(i64p), C.byref(tot))
+        if rc not in (OK, ESMALL):
+            raise MscdError(rc, "mscd_get_memberships")
+        return f[:N], stt[:N]
 
     def communities(self, scale: int):
         """(comm_ptr, comm_nodes, fitness, seed2comm)."""

@@ -129,3 +129,91 @@ def test_admission_by_memory_and_busy_graph(env):
         assert e.value.rc == mscd.EINVAL
     finally:
         ctx.serve_stop()
+
+
+def _max_overlap(starts, ends):
+    ev = sorted([(t, 1) for t in starts] + [(t, -1) for t in ends], key=lambda x: (x[0], x[1]))
+    cur = best = 0
+    for _, d in ev:
+        cur += d
+        best = max(best, cur)
+    return best
+
+
+def test_batches_overlap_on_device(env):
+    """Continuous batching: under a mixed load the batches of different
+    workers are on the GPU at the same time.  Each batch's device interval is
+    timed by CUDA events on its worker's stream (first copy in to last copy
+    out); at least two of them must overlap, and the server's own count of
+    the most batches in flight at once agrees with a sweep over the
+    intervals it reports."""
+    from paper_1301_0955_gb300 import mscd
+
+    ctx, graphs, gids = env
+    ctx.serve_start(workers=4, max_batch_units=4096)
+    try:
+        rng = np.random.default_rng(17)
+        scales = mscd.scales_logspaced(0.5, 1.0, 16)
+        qs = []
+        for i in range(48):
+            gi = i % 2
+            seeds = rng.integers(0, graphs[gi].n, int(rng.integers(512, 4097))).astype(np.int32)
+            qs.append((seeds, ctx.submit(gids[gi], seeds, float(scales[int(rng.integers(0, 16))]))))
+        for seeds, q in qs:
+            assert ctx.wait(q, 300) == mscd.Q_DONE
+            ctx.result(q, len(seeds))
+        st = ctx.serve_stats()
+        a, b = ctx.batch_intervals()
+    finally:
+        ctx.serve_stop()
+    assert len(a) == st["batches"] >= 2
+    assert (b >= a).all()
+    assert st["max_concurrent_batches"] == _max_overlap(a, b)
+    assert st["max_concurrent_batches"] >= 2 and st["overlap_us"] > 0
+
+
+def test_serving_graph_full_size(orc):
+    """One of the four 2,000,000-node serving graphs (mean degree 25, three
+    levels): queries at 4 of the 16 scales, plus one of 4096 seeds, served
+    concurrently; every returned list and fitness against the oracle."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import os
+
+    from paper_1301_0955_gb300 import build, mscd
+
+    build.build()
+    ctx = mscd.Context(0)
+    g = synth.config_graph(4)
+    assert g.n == 2_000_000
+    gid = ctx.load_csr(g.n, g.row_ptr, g.col)
+    G = orc.Graph(g.n, g.row_ptr, g.col)
+    scales = mscd.scales_logspaced(0.5, 1.0, 16)
+    rng = np.random.default_rng(23)
+    ctx.serve_start(workers=4, max_batch_units=65536)
+    try:
+        qs = []
+        for s in (0, 5, 10, 15):
+            for _ in range(2):
+                seeds = np.sort(rng.choice(g.n, 160, replace=False)).astype(np.int32)
+                qs.append((s, seeds, ctx.submit(gid, seeds, float(scales[s]))))
+        big = rng.choice(g.n, 4096, replace=False).astype(np.int32)
+        qs.append((8, big, ctx.submit(gid, big, float(scales[8]))))
+        out = []
+        for s, seeds, q in qs:
+            assert ctx.wait(q, 600) == mscd.Q_DONE
+            ptr, nodes, f, t, rc = ctx.result(q, len(seeds))
+            assert rc == mscd.OK
+            out.append((s, seeds, ptr, nodes, f))
+    finally:
+        ctx.serve_stop()
+    for s, seeds, ptr, nodes, f in out:
+        pick = np.arange(len(seeds)) if len(seeds) <= 160 else np.sort(rng.choice(len(seeds), 160, replace=False))
+        rc, optr, onodes, of, ost = orc.run(G, [scales[s]], seeds[pick], threads=os.cpu_count() or 1)
+        assert rc == 0
+        for t, j in enumerate(pick):
+            assert np.array_equal(nodes[ptr[j]:ptr[j + 1]], onodes[optr[t]:optr[t + 1]]), (s, int(seeds[j]))
+            assert f[j] == pytest.approx(of[t], rel=1e-12, abs=0)
+    ctx.free_graph(gid)
+    ctx.close()

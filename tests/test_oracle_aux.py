@@ -254,3 +254,42 @@ def test_nmi_hand_computed_two_covers(orc):
     b2 = (np.array([0, 3, 4], np.int64), np.array([0, 1, 2, 3], np.int32))
     want2 = 1.0 - 0.5 * ((1.5 - HY) + 0.5 * (0.5 / HY + 1.0))
     assert orc.nmi(4, *a, *b2) == pytest.approx(want2, abs=1e-15)
+
+
+def _random_cover(rng, n, k, lo, hi):
+    ptr, nodes = [0], []
+    for _ in range(k):
+        m = int(rng.integers(lo, min(hi, n) + 1))
+        nodes.append(np.sort(rng.choice(n, m, replace=False)))
+        ptr.append(ptr[-1] + m)
+    return np.array(ptr, np.int64), np.concatenate(nodes).astype(np.int32)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_nmi_indexed_equals_dense_definition(orc, seed):
+    """The indexed variant counts intersections through a node -> communities
+    index instead of intersecting every pair of lists; everything else is the
+    dense definition, so the two agree bit for bit (random overlapping covers,
+    small and large communities, whole-graph and disjoint ones, 1 and 4
+    threads)."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(5, 400))
+    X = _random_cover(rng, n, int(rng.integers(1, 40)), 1, max(2, n // int(rng.integers(1, 8))))
+    Y = _random_cover(rng, n, int(rng.integers(1, 40)), 1, max(2, n // int(rng.integers(1, 8))))
+    if seed % 3 == 0:  # a community of every node
+        Y = (np.append(Y[0], Y[0][-1] + n), np.concatenate([Y[1], np.arange(n, dtype=np.int32)]))
+    want = orc.nmi(n, *X, *Y)
+    for t in (1, 4):
+        got = orc.nmi_indexed(n, *X, *Y, threads=t)
+        assert got == want or (np.isnan(got) and np.isnan(want)), (seed, t, got, want)
+
+
+def test_nmi_indexed_hand_example(orc):
+    """The worked two-cover example (closed form above) through the indexed variant."""
+    import math
+
+    HY = 2.0 - 0.75 * math.log2(3.0)
+    want = 1.0 - 0.5 * ((1.5 - HY) + 0.5 / HY)
+    a = (np.array([0, 2], np.int64), np.array([0, 1], np.int32))
+    b = (np.array([0, 3], np.int64), np.array([0, 1, 2], np.int32))
+    assert orc.nmi_indexed(4, *a, *b) == pytest.approx(want, abs=1e-15)
