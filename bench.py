@@ -1,29 +1,32 @@
 #!/usr/bin/env python
 """Benchmark of the multi-scale LFK community-growth hot path on one GB300.
 
-Workload (one step): the 100,000-node LFR-style hierarchical graph (power-law
-degrees tau = 2.5, mean 20, max 200; community sizes 20..1000, tau = 1.5; two
-levels; mixing 0.3 / 0.1; unweighted), 20 log-spaced scales in [0.5, 1],
-every node a seed: graph checks and exact weights, growth of all 2,000,000
-(scale, seed) units, dedup per scale, NMI between successive scales.
+Workload (one step, the default): the 1,000,000-node three-level LFR-style
+hierarchical graph (power-law degrees tau = 2.5, mean 30, max 300; micro
+community sizes 20..1000, tau = 1.5, grouped 2-6 per level; mixing 0.3 / 0.2 /
+0.1; FP32 edge weights uniform in [0.5, 2]), 32 log-spaced scales in
+[0.5, 1], every node a seed: graph checks and exact weights, growth of all
+32,000,000 (scale, seed) units in one persistent run, dedup per scale, NMI
+between successive scales.
 
   value      seed expansions (units) per second, graph already resident in HBM
   e2e        the same through the C ABI from pinned host buffers, with the
              host->device copy of the graph and the device->host read of every
              scale's communities and the stability inside the timed region
-  roofline   growth kernel: algorithmic bytes (4 B per CSR entry scanned +
-             16 B per row visited) / growth time, against the measured HBM copy
-             bandwidth
+  roofline   growth kernels: algorithmic bytes (4 B per CSR entry scanned, plus
+             8 B for the exact weight on a weighted graph, + 16 B per row
+             visited) / growth time, against the measured HBM copy bandwidth
 
 --impl reference times the CPU oracle (the reference arm) on a
 bounded sample of the same workload.  Under torchrun every rank runs its own
 replica of the workload (weak scaling, no collective on the data path).
 
-Other workloads (--workload): uneven-batch (256 graphs of log-uniform size as
-one disjoint union, 16 scales), serve (query server on four 2M-node graphs,
-Poisson arrivals at fractions of saturation, p50/p99 latency), full (the
-paper's whole Alg. 2 on the 100k-node graph) and accuracy (scale ranges where
-planted levels are found, in the shape of the paper's Table 1).
+Other workloads (--workload): lfr-100k (the 100,000-node two-level graph, 20
+scales), uneven-batch (256 graphs of log-uniform size as one disjoint union,
+16 scales), serve (query server on four 2M-node graphs, Poisson arrivals at
+fractions of saturation, p50/p99 latency), full (the paper's whole Alg. 2 on
+the 100k-node graph) and accuracy (scale ranges where planted levels are
+found, in the shape of the paper's Table 1).
 """
 import argparse
 import hashlib
