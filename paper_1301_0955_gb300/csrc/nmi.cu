@@ -197,6 +197,12 @@ struct DirArgs {
     unsigned long long *n_spill;
     const i64 *toff;
     i32 *tkey, *tcnt;
+    i32 *tused;           // buckets each global table claimed, at the table's offset
+    unsigned int *tfill;  // per community of a chunk: buckets claimed
+    // work counter of the launch (zeroed before it): communities are taken
+    // one at a time as warps or CTAs free up, since their costs differ by
+    // orders of magnitude
+    unsigned long long *next;
 };
 
 // Warp per active A community: intersections with every B community it meets
@@ -209,7 +215,6 @@ __global__ void __launch_bounds__(NMI_WARPS * 32) pairs_smem(DirArgs a) {
     __shared__ unsigned short sused[NMI_WARPS][NMI_TABLE / 2];
     __shared__ int sfill[NMI_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const i64 warps = (i64)gridDim.x * NMI_WARPS;
     i32 *keys = skey[w];
     i32 *cnts = scnt[w];
     unsigned short *used = sused[w];
@@ -218,7 +223,11 @@ __global__ void __launch_bounds__(NMI_WARPS * 32) pairs_smem(DirArgs a) {
         cnts[t] = 0;
     }
     __syncwarp();
-    for (i64 q = (i64)blockIdx.x * NMI_WARPS + w; q < a.n_active; q += warps) {
+    for (;;) {
+        unsigned long long qq = 0;
+        if (lane == 0) qq = atomicAdd(a.next, 1ull);
+        const i64 q = (i64)__shfl_sync(FULL_MASK, qq, 0);
+        if (q >= a.n_active) break;
         const i32 k = a.active[q];
         if (lane == 0) sfill[w] = 0;
         __syncwarp();
@@ -282,11 +291,18 @@ constexpr int GLB_WARPS = 16;
 
 __global__ void __launch_bounds__(GLB_WARPS * 32) pairs_global(DirArgs a, const i64 *list, i64 nk) {
     __shared__ double wmin[GLB_WARPS];
+    __shared__ i64 rnext;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (i64 r = blockIdx.x; r < nk; r += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) rnext = (i64)atomicAdd(a.next, 1ull);
+        __syncthreads();
+        const i64 r = rnext;
+        if (r >= nk) break;
         const i32 k = a.active[list[r]];
         i32 *keys = a.tkey + a.toff[r];
         i32 *cnts = a.tcnt + a.toff[r];
+        i32 *used = a.tused + a.toff[r];
+        unsigned int *fill = a.tfill + r;
         const u32 tm = (u32)(a.toff[r + 1] - a.toff[r] - 1);
         for (i64 e = a.aptr[k] + w; e < a.aptr[k + 1]; e += GLB_WARPS) {
             const i32 u = a.anodes[e];
@@ -297,7 +313,10 @@ __global__ void __launch_bounds__(GLB_WARPS * 32) pairs_global(DirArgs a, const 
                     i32 cur = keys[h];
                     if (cur == -1) {
                         cur = atomicCAS(&keys[h], -1, l);
-                        if (cur == -1) cur = l;
+                        if (cur == -1) {
+                            used[atomicAdd(fill, 1u)] = (i32)h;
+                            cur = l;
+                        }
                     }
                     if (cur == l) {
                         atomicAdd(&cnts[h], 1);
@@ -311,9 +330,14 @@ __global__ void __launch_bounds__(GLB_WARPS * 32) pairs_global(DirArgs a, const 
         const i64 sa = a.aptr[k + 1] - a.aptr[k], n = a.acn[k];
         const double inv_n = 1.0 / (double)n;
         double bx = __builtin_huge_val();
-        for (u32 t = threadIdx.x; t <= tm; t += GLB_WARPS * 32) {
-            const i32 l = keys[t];
-            if (l >= 0) bx = min(bx, cond_candidate(cnts[t], sa, a.bptr[l + 1] - a.bptr[l], n, inv_n));
+        // only the claimed buckets, emptied again for the table's next user
+        const u32 nf = *(volatile unsigned int *)fill;
+        for (u32 t = threadIdx.x; t < nf; t += GLB_WARPS * 32) {
+            const i32 hh = used[t];
+            const i32 l = keys[hh];
+            bx = min(bx, cond_candidate(cnts[hh], sa, a.bptr[l + 1] - a.bptr[l], n, inv_n));
+            keys[hh] = -1;
+            cnts[hh] = 0;
         }
         for (int o = 16; o; o >>= 1) bx = min(bx, __shfl_xor_sync(FULL_MASK, bx, o));
         if (lane == 0) wmin[w] = bx;
@@ -341,11 +365,16 @@ __global__ void __launch_bounds__(BLK_WARPS * 32) pairs_block(DirArgs a, const i
     __shared__ int fill, over;
     __shared__ double wmin[BLK_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ i64 rnext;
     for (int t = threadIdx.x; t < BLK_TABLE; t += BLK_WARPS * 32) {
         keys[t] = -1;
         cnts[t] = 0;
     }
-    for (i64 r = blockIdx.x; r < nk; r += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) rnext = (i64)atomicAdd(a.next, 1ull);
+        __syncthreads();
+        const i64 r = rnext;
+        if (r >= nk) break;
         const i64 q = list[r];
         const i32 k = a.active[q];
         if (threadIdx.x == 0) {
@@ -564,16 +593,18 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
                   cudaStream_t st) {
     i64 *spill = nullptr, *spill2 = nullptr, *tsz = nullptr, *toff = nullptr, *dboff = nullptr, *bsize = nullptr;
     i32 *bpart = nullptr;
-    i32 *tkey = nullptr, *tcnt = nullptr, *big = nullptr;
+    i32 *tkey = nullptr, *tcnt = nullptr, *tused = nullptr, *big = nullptr;
+    unsigned int *tfill = nullptr;
     unsigned long long *cnt = nullptr, *amax = nullptr;
     int rc = MSCD_OK;
     do {
         if (n_active == 0) break;
         if ((rc = dev_alloc(&spill, n_active, st))) break;
-        if ((rc = dev_alloc(&cnt, 3, st))) break;
+        // spills, big-B count, spills of the block tier, then the launches' work counters
+        if ((rc = dev_alloc(&cnt, 6, st))) break;
         if ((rc = dev_alloc(&big, B.n_comms, st))) break;
         if ((rc = dev_alloc(&amax, P, st))) break;
-        if ((rc = cuda_status(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), st)))) break;
+        if ((rc = cuda_status(cudaMemsetAsync(cnt, 0, 6 * sizeof(unsigned long long), st)))) break;
         if ((rc = cuda_status(cudaMemsetAsync(amax, 0, (size_t)P * sizeof(unsigned long long), st)))) break;
         DirArgs a{};
         a.aptr = A.comm_ptr;
@@ -587,6 +618,7 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
         a.best = best;
         a.spill = spill;
         a.n_spill = cnt;
+        a.next = cnt + 3;
         pairs_smem<<<(unsigned)std::min<i64>((n_active + NMI_WARPS - 1) / NMI_WARPS, 152 * 3), NMI_WARPS * 32, 0,
                      st>>>(a); note_launch();
         active_max_size<<<GB, 256, 0, st>>>(A.comm_ptr, active, n_active, PA.cp, amax); note_launch();
@@ -603,6 +635,7 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
             if ((rc = cuda_status(cudaFuncSetAttribute(pairs_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                        (int)bsm))))
                 break;
+            a.next = cnt + 4;
             pairs_block<<<(unsigned)std::min<i64>(nk, 152), BLK_WARPS * 32, bsm, st>>>(a, spill, nk, spill2, cnt + 2); note_launch();
             unsigned long long h2 = 0;
             if ((rc = cuda_status(cudaMemcpyAsync(&h2, cnt + 2, sizeof(h2), cudaMemcpyDeviceToHost, st)))) break;
@@ -624,11 +657,18 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
             for (i64 v : hs) largest = std::max(largest, v);
             size_t fr = 0, tot = 0;
             cudaMemGetInfo(&fr, &tot);
-            const i64 budget = std::max<i64>(largest, std::min<i64>((i64)1 << 28, (i64)(fr / 8 / (2 * sizeof(i32)))));
+            const i64 budget = std::max<i64>(largest, std::min<i64>((i64)1 << 28, (i64)(fr / 8 / (3 * sizeof(i32)))));
             if ((rc = dev_alloc(&tkey, budget, st))) break;
             if ((rc = dev_alloc(&tcnt, budget, st))) break;
+            if ((rc = dev_alloc(&tused, budget, st))) break;
+            if ((rc = dev_alloc(&tfill, nk, st))) break;
+            // emptied once; each community empties the buckets it claimed
+            if ((rc = cuda_status(cudaMemsetAsync(tkey, 0xff, budget * sizeof(i32), st)))) break;
+            if ((rc = cuda_status(cudaMemsetAsync(tcnt, 0, budget * sizeof(i32), st)))) break;
             a.tkey = tkey;
             a.tcnt = tcnt;
+            a.tused = tused;
+            a.tfill = tfill;
             a.toff = toff;
             std::vector<i64> ho;
             for (i64 r0 = 0; r0 < nk && rc == MSCD_OK;) {
@@ -638,12 +678,12 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
                     ho.push_back(ho.back() + hs[r1]);
                     ++r1;
                 }
-                const i64 TT = ho.back();
                 if ((rc = cuda_status(cudaMemcpyAsync(toff, ho.data(), ho.size() * sizeof(i64), cudaMemcpyHostToDevice,
                                                       st))))
                     break;
-                if ((rc = cuda_status(cudaMemsetAsync(tkey, 0xff, TT * sizeof(i32), st)))) break;
-                if ((rc = cuda_status(cudaMemsetAsync(tcnt, 0, TT * sizeof(i32), st)))) break;
+                if ((rc = cuda_status(cudaMemsetAsync(tfill, 0, (r1 - r0) * sizeof(unsigned int), st)))) break;
+                if ((rc = cuda_status(cudaMemsetAsync(cnt + 5, 0, sizeof(unsigned long long), st)))) break;
+                a.next = cnt + 5;
                 pairs_global<<<(unsigned)std::min<i64>(r1 - r0, 152 * 4), GLB_WARPS * 32, 0, st>>>(a, list + r0,
                                                                                               r1 - r0);
                 note_launch();
@@ -699,6 +739,8 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
     if (toff) cudaFreeAsync(toff, st);
     if (tkey) cudaFreeAsync(tkey, st);
     if (tcnt) cudaFreeAsync(tcnt, st);
+    if (tused) cudaFreeAsync(tused, st);
+    if (tfill) cudaFreeAsync(tfill, st);
     if (bpart) cudaFreeAsync(bpart, st);
     if (bsize) cudaFreeAsync(bsize, st);
     if (dboff) cudaFreeAsync(dboff, st);
