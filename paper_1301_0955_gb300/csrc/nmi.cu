@@ -352,10 +352,10 @@ __global__ void __launch_bounds__(GLB_WARPS * 32) pairs_global(DirArgs a, const 
 }
 
 constexpr int BLK_WARPS = 16;
-constexpr int BLK_TABLE = 16384;  // shared-memory hash entries of one CTA
+constexpr int BLK_TABLE = 8192;  // shared-memory hash entries of one CTA (72 KB: 3 CTAs per SM)
 
 // CTA per community spilled by pairs_smem: its members are spread over the
-// warps, a 16384-entry shared-memory table counts the intersections; a
+// warps, an 8192-entry shared-memory table counts the intersections; a
 // community meeting more than half of that is listed for pairs_global.
 __global__ void __launch_bounds__(BLK_WARPS * 32) pairs_block(DirArgs a, const i64 *list, i64 nk, i64 *spill2,
                                                               unsigned long long *n_spill2) {
@@ -636,7 +636,11 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
                                                        (int)bsm))))
                 break;
             a.next = cnt + 4;
-            pairs_block<<<(unsigned)std::min<i64>(nk, 152), BLK_WARPS * 32, bsm, st>>>(a, spill, nk, spill2, cnt + 2); note_launch();
+            // as many CTAs as fit the SMs' shared memory
+            const i64 per_sm = std::max<i64>(1, (i64)(216 * 1024) / (i64)bsm);
+            pairs_block<<<(unsigned)std::min<i64>(nk, 152 * per_sm), BLK_WARPS * 32, bsm, st>>>(a, spill, nk, spill2,
+                                                                                           cnt + 2);
+            note_launch();
             unsigned long long h2 = 0;
             if ((rc = cuda_status(cudaMemcpyAsync(&h2, cnt + 2, sizeof(h2), cudaMemcpyDeviceToHost, st)))) break;
             if ((rc = cuda_status(cudaStreamSynchronize(st)))) break;
