@@ -51,7 +51,7 @@ int ctx_device_of(mscd_ctx *c);
 namespace {
 
 constexpr int NMI_WARPS = 8;
-constexpr int NMI_TABLE = 1024;  // shared-memory hash entries per warp
+constexpr int NMI_TABLE = 512;  // shared-memory hash entries per warp (6 CTAs of 8 warps per SM)
 
 __device__ __forceinline__ double hterm(i64 c, double inv_n) {
     if (c <= 0) return 0.0;
@@ -619,7 +619,7 @@ int one_direction(const ScaleResult &A, const ScaleResult &B, const Memberships 
         a.spill = spill;
         a.n_spill = cnt;
         a.next = cnt + 3;
-        pairs_smem<<<(unsigned)std::min<i64>((n_active + NMI_WARPS - 1) / NMI_WARPS, 152 * 3), NMI_WARPS * 32, 0,
+        pairs_smem<<<(unsigned)std::min<i64>((n_active + NMI_WARPS - 1) / NMI_WARPS, 152 * 6), NMI_WARPS * 32, 0,
                      st>>>(a); note_launch();
         active_max_size<<<GB, 256, 0, st>>>(A.comm_ptr, active, n_active, PA.cp, amax); note_launch();
         list_big<<<GB, 256, 0, st>>>(B.comm_ptr, B.n_comms, PB.cp, PB.cn, amax, big, cnt + 1); note_launch();
