@@ -30,16 +30,19 @@
 // difference); E = 2^-20 (1+alpha)(1+L) per key is above it.
 //
 // Queue argmax: the slots are split into groups of 32 and each group keeps an
-// upper bound of its largest key (raised by atomicMax when a key rises, left
-// stale when a key is removed).  A pop recomputes exactly every group whose
-// bound is within 2E of the largest bound, and repeats while the largest
-// bound drops; the best node is then in a recomputed group (a group left out
-// has a bound, hence a true maximum, below the true maximum minus 2E), so the
-// result is the exact argmax at the cost of a few groups.
+// upper bound of its largest key (raised by atomicMax when a key rises).  A
+// pop recomputes exactly every group whose bound is within 2E of the largest
+// bound, and repeats while the largest bound drops; the best node is then in
+// a recomputed group (a group left out has a bound, hence a true maximum,
+// below the true maximum minus 2E), so the result is the exact argmax at the
+// cost of a few groups.  Bounds are made exact again wherever the kernel
+// holds the keys anyway (the added node's group, groups the bulk rejection
+// visits), so that a pop rarely meets a stale one.
 //
 // State per warp: node slots (d_in, key, id with the member flag in its sign
 // bit; k_u is read from the graph's degree array, which every unit shares),
-// group bounds and an open-addressing hash node -> slot, in shared memory
+// a member list (slots in joining order, for the prune passes and the
+// output), group bounds and an open-addressing hash node -> slot, in shared memory
 // (first class) or in a global-memory arena (larger classes, run at high
 // occupancy so that the dependent steps of one unit overlap with those of
 // many others).  The hash table starts small and doubles (rehashing every
