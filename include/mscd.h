@@ -134,7 +134,9 @@ typedef struct mscd_run_stats {
 /* Text of a status code (static storage). */
 const char *mscd_strerror(int status);
 
-/* Library version, major*10000 + minor*100 + patch. */
+/* Library version, major*10000 + minor*100 + patch.  0.2.0 (200) added
+ * mscd_params.list_hash_bits, the last two fields of mscd_serve_stats and
+ * mscd_serve_batch_intervals; structs of 0.1.x have other sizes. */
 int mscd_version(void);
 
 /* Number of kernels this library has launched in the calling process so far

@@ -270,7 +270,7 @@ const char *mscd_strerror(int s) {
     }
 }
 
-int mscd_version(void) { return 100; }
+int mscd_version(void) { return 200; }
 
 int64_t mscd_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
