@@ -171,6 +171,66 @@ def test_bruteforce_local_optimum(orc, alpha):
     assert checked > 200
 
 
+@pytest.mark.parametrize("alpha", [1.0, 0.5, 0.75, 0.6180339887498949])
+def test_bruteforce_local_optimum_float_weights(orc, alpha):
+    """FP32 weights drawn uniformly from [0.5, 2] (the weighted workload's
+    distribution).  Every float is a dyadic rational, so scaling by the largest
+    denominator, computed here from the floats with Fraction, gives exact
+    integer weights; K and V must equal the oracle's statistics in its weight
+    unit, the result must be a local optimum under exact comparisons and never
+    above the best subset containing the seed."""
+    from fractions import Fraction
+
+    rng = random.Random(int(alpha * 7919))
+    nrng = np.random.default_rng(int(alpha * 7919))
+    checked = 0
+    for it in range(40):
+        n = rng.randint(4, 11)
+        edges = [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < rng.uniform(0.25, 0.6)]
+        if not edges:
+            continue
+        w32 = nrng.uniform(0.5, 2.0, len(edges)).astype(np.float32)
+        fr = [Fraction(float(x)) for x in w32]
+        L = max(f.denominator for f in fr)
+        wi = [int(f * L) for f in fr]  # exact integers in units of 1/L
+        g, rp, col = graph_from_edges(orc, n, edges, w32)
+        assert g.status == 0
+        unit = Fraction(2) ** g.info()["unit_exp"]
+        adj = [dict() for _ in range(n)]
+        for idx, (a, b) in enumerate(edges):
+            adj[a][b] = wi[idx]
+            adj[b][a] = wi[idx]
+        k = [sum(adj[u].values()) for u in range(n)]
+        for seed in range(n):
+            mem, f, st, rc = orc.grow(g, seed, alpha)
+            assert rc == 0
+            c = set(mem.tolist())
+            assert seed in c
+            K, V = kv(adj, k, c)
+            assert Fraction(K, L) == st["K"] * unit and Fraction(V, L) == st["V"] * unit
+            if K:
+                assert f == pytest.approx(float(Fraction(K, L)) / float(Fraction(V, L)) ** alpha, rel=1e-13)
+            for u in range(n):
+                if u in c:
+                    if u == seed:
+                        continue
+                    K2, V2 = kv(adj, k, c - {u})
+                else:
+                    K2, V2 = kv(adj, k, c | {u})
+                assert not f_greater(K2, V2, K, V, alpha), (edges, seed, alpha, sorted(c), u)
+            if n <= 9:
+                others = [u for u in range(n) if u != seed]
+                best = (0, 1)
+                for r in range(len(others) + 1):
+                    for sub in itertools.combinations(others, r):
+                        K2, V2 = kv(adj, k, set(sub) | {seed})
+                        if f_greater(K2, V2, *best, alpha):
+                            best = (K2, V2)
+                assert not f_greater(K, V, *best, alpha)
+            checked += 1
+    assert checked > 150
+
+
 def structured_graphs():
     """Small graphs whose symmetry makes ranking and fitness ties common: the
     smaller-id rule and the strict tests decide most steps."""
